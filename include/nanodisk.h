@@ -1,0 +1,179 @@
+/*
+ * nanodisk.h -- C ABI of the GB300 thin-nanodisk micromagnetics library
+ * (libnanodisk.so).
+ *
+ * The library computes the per-time-step effective field of thin circular
+ * ferromagnetic disks discretised into a x a x L cells, following Wysin &
+ * Figueiredo, "Thermal vortex dynamics in thin circular ferromagnetic
+ * nanodisks" (2012):
+ *   - the demagnetisation field of the thin-film Green's tensor (Sec. II.B),
+ *     applied as a zero-padded FFT convolution over the square grid masked to
+ *     the disk, plus the nearest-neighbour exchange field (Eq. Bi);
+ *   - the Landau-Lifshitz equation with damping, stepped with RK4 at T = 0
+ *     (Sec. III.A) or with the stochastic Heun scheme of the Langevin
+ *     equation at T > 0 (Eq. LV, Sec. III.C);
+ *   - the energy of Eq. Hmm, the vortex-core estimator of Sec. IV, the
+ *     analytic vortex profile of Sec. IV, and the average magnetisation.
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * Units.  Physical inputs are SI (metres, A/m, J/m, seconds, kelvin).  Fields
+ * returned by the library are the dimensionless induction b_i of Eq. Bi (unit
+ * B0 = 2A/(a^2 Ms)); energies are in units of J = 2AL of the replica's disk.
+ *
+ * Grid.  A disk of radius R and cell edge a has D = round(2R/a) cells per
+ * side.  Cell (i, j) (column i = x index, row j = y index) has its centre at
+ * ((i - (D-1)/2) a, (j - (D-1)/2) a) and belongs to the disk iff that centre
+ * lies within R.  The FFT grid side P is the smallest power of two >= 2D - 1
+ * (at least 16), which makes the circular convolution equal the linear one.
+ *
+ * State layout.  One handle holds B replicas (disk-major: the replicas of disk
+ * 0 first).  A state buffer is one contiguous array of the handle's precision
+ * (float for ND_FP32, double for ND_FP64); replica r occupies
+ * [3][D_r][Dpad_r] elements starting at the offset nd_replica_layout reports,
+ * where Dpad_r = D_r rounded up to a multiple of 4 and components are x, y, z.
+ * Cells outside the disk read as zero (any value stored there is ignored) and
+ * are written as zero or left unchanged; padding columns are never touched.
+ *
+ * Pointers.  Array arguments named m or b may be device pointers or host
+ * pointers (pageable or pinned); the library inspects each.  With a host
+ * pointer the call copies the data to a device staging buffer, runs, copies
+ * results back, and returns after synchronising the stream.  With device
+ * pointers the call is asynchronous on `stream` (a cudaStream_t, NULL for the
+ * legacy default stream) unless it returns host scalars, in which case it
+ * synchronises `stream` before returning.  Scalar outputs (E_out, Xc_out, ...)
+ * are always host pointers.  The caller owns every buffer it passes; the
+ * handle owns its spectral kernels, twiddle tables and scratch.
+ *
+ * Errors.  Every call returns ND_OK (0) or a positive ND_ERR_* code; no
+ * exception crosses the ABI.  nd_last_error() returns a description of the
+ * most recent failure on the calling thread.  A handle is not thread-safe and
+ * calls on one handle must be ordered (one stream, or synchronised).
+ */
+#ifndef NANODISK_H
+#define NANODISK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ND_OK 0
+#define ND_ERR_ARG 1            /* invalid argument or unsupported size */
+#define ND_ERR_CUDA 2           /* a CUDA runtime call failed */
+#define ND_ERR_NOT_CONVERGED 3  /* relaxation hit max_iter */
+#define ND_ERR_NO_VORTEX 4      /* no plaquette with winding +1 */
+#define ND_ERR_TIMEOUT 5        /* a bounded device-side wait expired */
+#define ND_ERR_NAN 6            /* a non-finite value appeared in the state */
+
+#define ND_FP32 0               /* float state and fields, FP64 energies and core sums */
+#define ND_FP64 1               /* double everywhere */
+
+typedef struct nd_handle nd_handle;
+
+/* One disk geometry and material (SI).  hext is the uniform external field
+ * H_ext in A/m (Eq. Hmm); alpha the damping of Sec. III.A; polarity (+1/-1)
+ * and chirality (+1 counter-clockwise, -1 clockwise) are used by
+ * nd_init_vortex only. */
+typedef struct {
+    double R, L, a;
+    double Ms, A, gamma;
+    double alpha;
+    double hext[3];
+    int polarity, chirality;
+} nd_disk_desc;
+
+/* Create a handle for n_disks geometries with replicas_per_disk[d] replicas
+ * each (replicas_per_disk may be NULL: one replica per disk).  Builds each
+ * disk's mask and its spectral kernel from the thin-film Green's tensor of
+ * Sec. II.B (in-plane and out-of-plane components averaged over the
+ * thickness, cell self terms -N_x, -N_x, -N_z of a cylinder of radius
+ * a/sqrt(pi)) with the exchange stencil folded in.  Requires D >= 1 and
+ * P <= 1024.  On success *out receives the handle; the call synchronises the
+ * current device. */
+int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_per_disk, int precision,
+                   nd_handle **out);
+
+/* Release the handle and everything it owns.  NULL is accepted. */
+void nd_destroy(nd_handle *h);
+
+/* Description of the last error on this thread ("" if none). */
+const char *nd_last_error(void);
+
+/* Number of replicas and the total number of elements of a state buffer. */
+int nd_get_info(const nd_handle *h, int *n_replicas, long long *state_elems);
+
+/* Layout of replica r: grid side D, padded row Dpad, FFT side P, element
+ * offset of its [3][D][Dpad] block in a state buffer, and its active cells
+ * (cells inside the disk).  Any output pointer may be NULL. */
+int nd_replica_layout(const nd_handle *h, int r, int *D, int *Dpad, int *P, long long *offset, int *n_cells);
+
+/* Copy disk d's mask ([D][D] bytes, 1 inside the disk) to host memory. */
+int nd_disk_mask(const nd_handle *h, int d, unsigned char *mask_out);
+
+/* Units of disk d (Sec. III.A): out[0] lambda_ex (m), out[1] a^2/lambda_ex^2,
+ * out[2] B0 (T), out[3] t0 = 1/(gamma B0) (s), out[4] J = 2AL (J),
+ * out[5] N_x, out[6] N_z, out[7] cells inside the disk. */
+int nd_units(const nd_handle *h, int d, double out[8]);
+
+/* Rebuild disk d's spectral kernel (Sec. II.B, "FFT of the Green's matrix,
+ * done only once").  Gq == NULL rebuilds it from the paper's closed forms.
+ * Otherwise Gq is a host array [4][D][D] of a^2 G at cell displacements
+ * (dx, dy) >= 0, components xx, yy, xy, zz, self terms at [.][0][0], extended
+ * to negative displacements by the tensor's symmetry (xx, yy, zz even in both
+ * axes, xy odd in both).  Synchronises the device. */
+int nd_set_green_tensor(nd_handle *h, int d, const double *Gq);
+
+/* Per-replica damping alpha (host array [B]); replaces the disks' values. */
+int nd_set_damping(nd_handle *h, const double *alpha);
+
+/* b <- effective induction of Eq. Bi for every replica's state m:
+ * b_i = sum_{j in z(i), j in disk} m_j + (a^2/lambda_ex^2)(h_ext + h^M_i).
+ * b has the state layout; cells outside the disks are written as zero. */
+int nd_effective_field(nd_handle *h, const void *m, void *b, void *stream);
+
+/* Energy of Eq. Hmm for every replica, in units of J = 2AL, evaluated with a
+ * double-precision field and double-precision sums whatever the handle's
+ * precision: E_out[r] = -{ sum_pairs m_i . m_j + (a^2/lambda^2) sum_i
+ * (h_ext + h^M_i / 2) . m_i }.  dEdL_out must be NULL (reserved).
+ * E_out is a host array [B]; the call synchronises `stream`. */
+int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void *stream);
+
+/* n_steps classical RK4 steps of dm/dtau = m x b - alpha m x (m x b)
+ * (Sec. III.A) for every replica, with the full field at all four stages
+ * and |m_i| = 1 restored after each step; dtau = gamma B0 dt_seconds.
+ * m is updated in place. */
+int nd_step_rk4(nd_handle *h, void *m, long long n_steps, double dt_seconds, void *stream);
+
+/* n_steps stochastic Heun steps of the Langevin equation (Eq. LV, Sec.
+ * III.C): g = b dtau + sigma_s w, dm = m x [g - alpha m x g], Euler predictor
+ * and trapezoid corrector with the same w, |m| = 1 restored after each
+ * stage, sigma_s = sqrt(2 alpha T~ dtau), T~ = k_B T_kelvin[r] / J.
+ * w_i are three standard normals per cell drawn from Philox4x32-10 with
+ * key = seed[r] and counter = (cell index j*D+i, step, 0) where step runs from
+ * step0 to step0 + n_steps - 1 (Box-Muller on the two word pairs), so a run
+ * split into several calls is bit-identical to one call.  T_kelvin and seed
+ * are host arrays [B]; T_kelvin[r] == 0 gives deterministic Heun. */
+int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, const double *T_kelvin,
+                 const unsigned long long *seed, unsigned long long step0, void *stream);
+
+/* Analytic q = +1 vortex centred at X0[r] = (x0, y0) metres (host array
+ * [B][2]) for every replica (Sec. IV profile): in-plane angle atan2(y - y0,
+ * x - x0) + chirality pi/2, m_z = polarity exp(-rho^2/lambda_ex^2), |m| = 1. */
+int nd_init_vortex(nd_handle *h, void *m, const double *X0, void *stream);
+
+/* Vortex core position (Sec. IV) of every replica: the vorticity centre is
+ * the plaquette with winding +1 (largest m_z^2 sum of its corners on ties);
+ * Xc_out[r] = sum (m_z)^2 r_i / sum (m_z)^2 over disk cells within
+ * 4 lambda_ex of it, in metres (host array [B][2]).  status[r] (host [B],
+ * may be NULL) is 0 or ND_ERR_NO_VORTEX.  Returns ND_ERR_NO_VORTEX if any
+ * replica has none.  Synchronises `stream`. */
+int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, void *stream);
+
+/* Average magnetisation <m> = (1/N) sum_i m_i over each disk (Sec. IV);
+ * out is a host array [B][3].  Synchronises `stream`. */
+int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NANODISK_H */

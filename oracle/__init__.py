@@ -82,6 +82,7 @@ def lib():
                 "ndo_demag": (None, [_P, _P, _P]),
                 "ndo_field": (None, [_P, _P, _P]),
                 "ndo_field_parts": (None, [_P, _P, _P, _P]),
+                "ndo_field_at": (None, [_P, _P, _P, _I, _P]),
                 "ndo_energy": (_D, [_P, _P]),
                 "ndo_pair_count": (ctypes.c_long, [_P]),
                 "ndo_llg_rhs": (None, [_P, _P, _P, _D, _P]),
@@ -227,6 +228,14 @@ class Model:
         b = np.zeros_like(m)
         lib().ndo_field(self._buf, _ptr(m), _ptr(b))
         return b
+
+    def field_at(self, m, cells):
+        """Induction at flat cell indices j*D+i (direct sum), shape (n, 3)."""
+        m = self._state(m)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((len(cells), 3))
+        lib().ndo_field_at(self._buf, _ptr(m), _ptr(cells), len(cells), _ptr(out))
+        return out
 
     def field_parts(self, m):
         m = self._state(m)

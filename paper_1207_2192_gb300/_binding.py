@@ -1,0 +1,204 @@
+"""ctypes binding of libnanodisk.so (include/nanodisk.h).
+
+Argument marshalling only: every step of the computation runs inside the CUDA
+library.  The functions keep the C names; pointers may be torch CUDA tensors,
+numpy arrays (host buffers) or raw integers.  If the library cannot be built
+or loaded the import fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ND_OK, ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NOT_CONVERGED, ND_ERR_NO_VORTEX, ND_ERR_TIMEOUT, ND_ERR_NAN = range(7)
+ND_FP32, ND_FP64 = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class NDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnanodisk error {code}: {msg}")
+        self.code = code
+
+
+class nd_disk_desc(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("L", ctypes.c_double), ("a", ctypes.c_double),
+                ("Ms", ctypes.c_double), ("A", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("hext", ctypes.c_double * 3),
+                ("polarity", ctypes.c_int), ("chirality", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+_ULL = ctypes.c_ulonglong
+
+SIGNATURES = {
+    "nd_create_disk": (_I, [_P, _I, _P, _I, _P]),
+    "nd_destroy": (None, [_P]),
+    "nd_last_error": (ctypes.c_char_p, []),
+    "nd_get_info": (_I, [_P, _P, _P]),
+    "nd_replica_layout": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+    "nd_disk_mask": (_I, [_P, _I, _P]),
+    "nd_units": (_I, [_P, _I, _P]),
+    "nd_set_green_tensor": (_I, [_P, _I, _P]),
+    "nd_set_damping": (_I, [_P, _P]),
+    "nd_effective_field": (_I, [_P, _P, _P, _P]),
+    "nd_energy": (_I, [_P, _P, _P, _P, _P]),
+    "nd_step_rk4": (_I, [_P, _P, _LL, _D, _P]),
+    "nd_step_heun": (_I, [_P, _P, _LL, _D, _P, _P, _ULL, _P]),
+    "nd_init_vortex": (_I, [_P, _P, _P, _P]),
+    "nd_vortex_core": (_I, [_P, _P, _P, _P, _P]),
+    "nd_mean_m": (_I, [_P, _P, _P, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build: bool = True):
+    """Load (building first if stale) libnanodisk.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise ImportError(f"libnanodisk.so not found at {path}; run paper_1207_2192_gb300.build.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor, numpy array, ctypes object or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return ctypes.cast(x, ctypes.c_void_p).value
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc):
+    if rc != ND_OK:
+        raise NDError(rc, lib().nd_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------- C names
+
+def nd_create_disk(disks, replicas_per_disk=None, precision=ND_FP32):
+    arr = (nd_disk_desc * len(disks))(*disks)
+    rep = None if replicas_per_disk is None else (ctypes.c_int * len(disks))(*replicas_per_disk)
+    h = ctypes.c_void_p()
+    _check(lib().nd_create_disk(ctypes.cast(arr, _P), len(disks), ctypes.cast(rep, _P) if rep else None, precision,
+                                ctypes.byref(h)))
+    return h.value
+
+
+def nd_destroy(h):
+    lib().nd_destroy(h)
+
+
+def nd_last_error():
+    return lib().nd_last_error().decode()
+
+
+def nd_get_info(h):
+    n, e = ctypes.c_int(), ctypes.c_longlong()
+    _check(lib().nd_get_info(h, ctypes.byref(n), ctypes.byref(e)))
+    return n.value, e.value
+
+
+def nd_replica_layout(h, r):
+    D, Dp, P, off, C = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+    _check(lib().nd_replica_layout(h, r, ctypes.byref(D), ctypes.byref(Dp), ctypes.byref(P), ctypes.byref(off),
+                                   ctypes.byref(C)))
+    return dict(D=D.value, Dpad=Dp.value, P=P.value, offset=off.value, cells=C.value)
+
+
+def nd_disk_mask(h, d, D):
+    out = np.zeros((D, D), dtype=np.uint8)
+    _check(lib().nd_disk_mask(h, d, _ptr(out)))
+    return out
+
+
+def nd_units(h, d):
+    out = np.zeros(8)
+    _check(lib().nd_units(h, d, _ptr(out)))
+    return out
+
+
+def nd_set_green_tensor(h, d, Gq=None):
+    g = None if Gq is None else np.ascontiguousarray(Gq, dtype=np.float64)
+    _check(lib().nd_set_green_tensor(h, d, _ptr(g)))
+
+
+def nd_set_damping(h, alpha):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    _check(lib().nd_set_damping(h, _ptr(a)))
+
+
+def nd_effective_field(h, m, b, stream=None):
+    _check(lib().nd_effective_field(h, _ptr(m), _ptr(b), _stream(stream)))
+
+
+def nd_energy(h, m, nrep, stream=None):
+    E = np.zeros(nrep)
+    _check(lib().nd_energy(h, _ptr(m), _ptr(E), None, _stream(stream)))
+    return E
+
+
+def nd_step_rk4(h, m, n_steps, dt_seconds, stream=None):
+    _check(lib().nd_step_rk4(h, _ptr(m), n_steps, dt_seconds, _stream(stream)))
+
+
+def nd_step_heun(h, m, n_steps, dt_seconds, T_kelvin, seed, step0=0, stream=None):
+    T = np.ascontiguousarray(T_kelvin, dtype=np.float64)
+    s = np.ascontiguousarray(seed, dtype=np.uint64)
+    _check(lib().nd_step_heun(h, _ptr(m), n_steps, dt_seconds, _ptr(T), _ptr(s), step0, _stream(stream)))
+
+
+def nd_init_vortex(h, m, X0, stream=None):
+    X = np.ascontiguousarray(X0, dtype=np.float64)
+    _check(lib().nd_init_vortex(h, _ptr(m), _ptr(X), _stream(stream)))
+
+
+def nd_vortex_core(h, m, nrep, stream=None, check=False):
+    Xc = np.zeros((nrep, 2))
+    st = np.zeros(nrep, dtype=np.int32)
+    rc = lib().nd_vortex_core(h, _ptr(m), _ptr(Xc), _ptr(st), _stream(stream))
+    if rc not in (ND_OK, ND_ERR_NO_VORTEX) or (check and rc != ND_OK):
+        _check(rc)
+    return Xc, st
+
+
+def nd_mean_m(h, m, nrep, stream=None):
+    out = np.zeros((nrep, 3))
+    _check(lib().nd_mean_m(h, _ptr(m), _ptr(out), _stream(stream)))
+    return out

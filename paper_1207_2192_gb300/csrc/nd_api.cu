@@ -1,0 +1,641 @@
+// nd_api.cu -- the C ABI (include/nanodisk.h): handle, geometry and units on
+// the host, device memory, staging of host buffers, and dispatch of each call
+// to the fused on-chip kernel or to the global-memory path per FFT size class.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/nanodisk.h"
+#include "nd_common.cuh"
+#include "nd_kernels.h"
+
+using namespace nd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define ND_CUDA(call)                                                                                      \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) return fail(ND_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+const double kMu0 = 4.0e-7 * M_PI;   // vacuum permeability (SI)
+const double kBoltzmann = 1.380649e-23;
+
+struct DiskInfo {
+    nd_disk_desc desc;
+    int D = 0, Dpad = 0, P = 0, C = 0;
+    double lambda = 0, cfac = 0, B0 = 0, t0 = 0, J = 0, Nx = 0, Nz = 0;
+    double h[3] = {0, 0, 0};   // H_ext / Ms
+    std::vector<unsigned char> mask;
+    unsigned char *mask_d = nullptr;
+    double *ghat64 = nullptr;  // [P/2+1][P/2+1][4]
+    float *ghat32 = nullptr;
+};
+
+struct SizeClass {
+    int P = 0, maxD = 0, maxDpad = 0;
+    std::vector<int> reps;     // replica indices
+    int *work_d = nullptr;     // device copy of reps
+    bool fused_main = false;   // fused kernel in the handle precision
+    bool fused_fp64 = false;   // fused kernel in FP64 (energy)
+    size_t smem_main = 0, smem_fp64 = 0;
+};
+
+int next_pow2_at_least(int n)
+{
+    int p = 16;
+    while (p < n) p *= 2;
+    return p;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct nd_handle {
+    int prec = ND_FP32;
+    int device = 0;
+    size_t elt = 4;                       // bytes per state element
+    std::vector<DiskInfo> disks;
+    std::vector<int> rep_disk;
+    std::vector<long long> rep_off;
+    std::vector<long long> rep_spec_off;  // complex words
+    long long state_elems = 0;
+    long long spec_words = 0;
+    std::vector<double> alpha;
+    std::vector<SizeClass> classes;
+    static constexpr int kSlots = 4;      // ring of pinned parameter blocks
+    Replica *reps_h = nullptr;            // current slot (points into reps_ring)
+    Replica *reps_ring = nullptr;         // pinned [kSlots][B]
+    cudaEvent_t slot_ev[kSlots] = {};
+    int slot = 0;
+    Replica *reps_d = nullptr;
+    std::map<int, void *> tw64, tw32;     // P -> length-P twiddle tables
+    void *acc = nullptr;                  // handle-precision scratch (state layout)
+    void *ms = nullptr;                   // handle-precision stage state (global path)
+    void *spec = nullptr;                 // spectrum scratch (global path), sized for FP64
+    void *stage_in = nullptr, *stage_out = nullptr;   // staging of host buffers
+    double *y64 = nullptr, *ms64 = nullptr;           // FP64 copies (energy of FP32 handles)
+    double *red_d = nullptr;              // [B] reductions
+    double *red_h = nullptr;              // pinned [B * 4]
+    double *aux_d = nullptr;              // [B * 4] small per-replica inputs/outputs
+    int *aux_i = nullptr;                 // [B * 2]
+    size_t max_smem = 0;
+};
+
+static int setup_class_paths(nd_handle *h)
+{
+    for (auto &c : h->classes) {
+        c.smem_main = fused_smem(c.P, h->prec, c.maxD, c.maxDpad);
+        c.fused_main = c.smem_main != (size_t)-1 && c.smem_main <= h->max_smem;
+        c.smem_fp64 = fused_smem(c.P, ND_PREC_FP64, c.maxD, c.maxDpad);
+        c.fused_fp64 = c.smem_fp64 != (size_t)-1 && c.smem_fp64 <= h->max_smem;
+    }
+    return ND_OK;
+}
+
+// Parameter blocks go through a ring of pinned host slots: a slot is reused
+// only after the copy that last read it has executed.
+static void next_slot(nd_handle *h)
+{
+    h->slot = (h->slot + 1) % nd_handle::kSlots;
+    cudaEventSynchronize(h->slot_ev[h->slot]);
+    h->reps_h = h->reps_ring + (size_t)h->slot * h->rep_disk.size();
+}
+
+static void upload_reps(nd_handle *h, cudaStream_t st)
+{
+    cudaMemcpyAsync(h->reps_d, h->reps_h, sizeof(Replica) * h->rep_disk.size(), cudaMemcpyHostToDevice, st);
+    cudaEventRecord(h->slot_ev[h->slot], st);
+}
+
+static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const double *Tk,
+                      const unsigned long long *seed, unsigned long long step0)
+{
+    const int B = (int)h->rep_disk.size();
+    next_slot(h);
+    for (int r = 0; r < B; ++r) {
+        const DiskInfo &d = h->disks[h->rep_disk[r]];
+        Replica &R = h->reps_h[r];
+        R.D = d.D;
+        R.Dpad = d.Dpad;
+        R.disk = h->rep_disk[r];
+        R.state_off = h->rep_off[r];
+        R.spec_off = h->rep_spec_off[r];
+        R.Ghat = fp64_kernel ? (const void *)d.ghat64 : (const void *)d.ghat32;
+        R.mask = d.mask_d;
+        for (int k = 0; k < 3; ++k) R.chext[k] = d.cfac * d.h[k];
+        R.alpha = h->alpha[r];
+        R.dtau = d.desc.gamma * d.B0 * dt_seconds;
+        double Ts = Tk ? kBoltzmann * Tk[r] / d.J : 0.0;
+        R.sigma = sqrt(2.0 * R.alpha * Ts * R.dtau);
+        R.flags = (R.sigma > 0.0) ? 1 : 0;
+        R.seed = seed ? seed[r] : 0ull;
+        R.step0 = step0;
+    }
+}
+
+// Run one mode over all replicas.  fp64 selects the FP64 kernels (with y a
+// double buffer of the state layout), otherwise the handle precision.
+static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st)
+{
+    const int prec = fp64 ? ND_PREC_FP64 : (h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32);
+    for (auto &c : h->classes) {
+        LaunchArgs a;
+        a.mode = mode;
+        a.reps = h->reps_d;
+        a.work = c.work_d;
+        a.nwork = (int)c.reps.size();
+        a.y = y;
+        a.out = out;
+        a.red = h->red_d;
+        a.nsteps = nsteps;
+        a.step_base = 0;
+        a.stream = st;
+        a.tw = (prec == ND_PREC_FP64) ? h->tw64[c.P] : h->tw32[c.P];
+        const bool fused = fp64 ? c.fused_fp64 : c.fused_main;
+        if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
+        if (fused) {
+            a.smem = fp64 ? c.smem_fp64 : c.smem_main;
+            ND_CUDA(launch_fused(c.P, prec, a));
+        } else {
+            a.ms = fp64 ? (void *)h->ms64 : h->ms;
+            a.spec = h->spec;
+            ND_CUDA(launch_global(c.P, prec, a, c.maxD));
+        }
+    }
+    return ND_OK;
+}
+
+static int ensure_alloc(void **p, size_t bytes)
+{
+    if (*p) return ND_OK;
+    ND_CUDA(cudaMalloc(p, bytes));
+    return ND_OK;
+}
+
+static int check_handle(const nd_handle *h)
+{
+    if (!h) return fail(ND_ERR_ARG, "null handle");
+    return ND_OK;
+}
+
+// Prepare a state argument: device pointers pass through; host pointers are
+// copied into a staging buffer.
+static int stage_in(nd_handle *h, const void *m, void **dev, bool copy, cudaStream_t st, void **slot)
+{
+    if (!m) return fail(ND_ERR_ARG, "null state pointer");
+    if (is_device_ptr(m)) {
+        *dev = const_cast<void *>(m);
+        return ND_OK;
+    }
+    size_t bytes = (size_t)h->state_elems * h->elt;
+    int rc = ensure_alloc(slot, bytes);
+    if (rc) return rc;
+    if (copy) ND_CUDA(cudaMemcpyAsync(*slot, m, bytes, cudaMemcpyHostToDevice, st));
+    *dev = *slot;
+    return ND_OK;
+}
+
+static int stage_out(nd_handle *h, void *m, const void *dev, cudaStream_t st)
+{
+    if (dev == m) return ND_OK;
+    ND_CUDA(cudaMemcpyAsync(m, dev, (size_t)h->state_elems * h->elt, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    return ND_OK;
+}
+
+extern "C" {
+
+const char *nd_last_error(void) { return g_err.c_str(); }
+
+int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_per_disk, int precision,
+                   nd_handle **out)
+{
+    if (!out) return fail(ND_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!disks || n_disks < 1) return fail(ND_ERR_ARG, "need at least one disk");
+    if (precision != ND_FP32 && precision != ND_FP64) return fail(ND_ERR_ARG, "precision must be ND_FP32 or ND_FP64");
+    nd_handle *h = new nd_handle();
+    h->prec = precision;
+    h->elt = precision == ND_FP64 ? 8 : 4;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return fail(ND_ERR_CUDA, "no CUDA device"); }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->max_smem = (size_t)optin;
+    // twiddle constants exp(-2 pi i k / 32)
+    {
+        double re[32], im[32];
+        for (int k = 0; k < 32; ++k) { re[k] = cos(2.0 * M_PI * k / 32.0); im[k] = -sin(2.0 * M_PI * k / 32.0); }
+        if (upload_twiddle_constants(re, im) != cudaSuccess) { delete h; return fail(ND_ERR_CUDA, "twiddle upload failed"); }
+    }
+    long long off = 0, soff = 0;
+    for (int d = 0; d < n_disks; ++d) {
+        const nd_disk_desc &ds = disks[d];
+        if (!(ds.R > 0 && ds.L > 0 && ds.a > 0 && ds.Ms > 0 && ds.A > 0 && ds.gamma > 0)) {
+            nd_destroy(h);
+            return fail(ND_ERR_ARG, "disk " + std::to_string(d) + ": R, L, a, Ms, A, gamma must be positive");
+        }
+        DiskInfo di;
+        di.desc = ds;
+        di.D = (int)floor(2.0 * ds.R / ds.a + 0.5);
+        if (di.D < 1) { nd_destroy(h); return fail(ND_ERR_ARG, "disk smaller than one cell"); }
+        di.Dpad = (di.D + 3) / 4 * 4;
+        di.P = next_pow2_at_least(2 * di.D - 1);
+        if (di.P > 1024) { nd_destroy(h); return fail(ND_ERR_ARG, "disk too large: padded grid above 1024"); }
+        di.lambda = sqrt(2.0 * ds.A / (kMu0 * ds.Ms * ds.Ms));
+        di.cfac = ds.a * ds.a / (di.lambda * di.lambda);
+        di.B0 = 2.0 * ds.A / (ds.a * ds.a * ds.Ms);
+        di.t0 = 1.0 / (ds.gamma * di.B0);
+        di.J = 2.0 * ds.A * ds.L;
+        const double ro = ds.a / sqrt(M_PI), q = sqrt(ds.L * ds.L + ro * ro);
+        di.Nz = (ds.L + ro - q) / ds.L;
+        di.Nx = (q - ro) / (2.0 * ds.L);
+        for (int k = 0; k < 3; ++k) di.h[k] = ds.hext[k] / ds.Ms;
+        di.mask.assign((size_t)di.D * di.D, 0);
+        const double rr = (ds.R / ds.a) * (ds.R / ds.a);
+        for (int j = 0; j < di.D; ++j)
+            for (int i = 0; i < di.D; ++i) {
+                const double x = i - 0.5 * (di.D - 1), y = j - 0.5 * (di.D - 1);
+                const bool in = (x * x + y * y) <= rr;
+                di.mask[(size_t)j * di.D + i] = in;
+                di.C += in;
+            }
+        const int nr = replicas_per_disk ? replicas_per_disk[d] : 1;
+        if (nr < 0) { nd_destroy(h); return fail(ND_ERR_ARG, "negative replica count"); }
+        for (int k = 0; k < nr; ++k) {
+            h->rep_disk.push_back(d);
+            h->rep_off.push_back(off);
+            h->rep_spec_off.push_back(soff);
+            h->alpha.push_back(ds.alpha);
+            off += 3LL * di.D * di.Dpad;
+            soff += (long long)spec_words(di.P, di.D);
+        }
+        h->disks.push_back(std::move(di));
+    }
+    const int B = (int)h->rep_disk.size();
+    if (B < 1) { nd_destroy(h); return fail(ND_ERR_ARG, "no replicas"); }
+    h->state_elems = off;
+    h->spec_words = soff;
+    // size classes by P
+    std::map<int, int> cls;
+    for (int r = 0; r < B; ++r) {
+        const DiskInfo &d = h->disks[h->rep_disk[r]];
+        auto it = cls.find(d.P);
+        if (it == cls.end()) {
+            cls[d.P] = (int)h->classes.size();
+            SizeClass c;
+            c.P = d.P;
+            h->classes.push_back(c);
+            it = cls.find(d.P);
+        }
+        SizeClass &c = h->classes[it->second];
+        c.reps.push_back(r);
+        c.maxD = std::max(c.maxD, d.D);
+        c.maxDpad = std::max(c.maxDpad, d.Dpad);
+    }
+    int rc = setup_class_paths(h);
+    if (rc) { nd_destroy(h); return rc; }
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        nd_destroy(h);
+        return fail(ND_ERR_CUDA, m);
+    };
+    cudaError_t e;
+    for (auto &c : h->classes) {
+        if ((e = cudaMalloc(&c.work_d, sizeof(int) * c.reps.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMemcpy(c.work_d, c.reps.data(), sizeof(int) * c.reps.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy");
+        if (!h->tw64.count(c.P)) {
+            std::vector<double> t64(2 * c.P);
+            std::vector<float> t32(2 * c.P);
+            for (int k = 0; k < c.P; ++k) {
+                t64[2 * k] = cos(2.0 * M_PI * k / c.P);
+                t64[2 * k + 1] = -sin(2.0 * M_PI * k / c.P);
+                t32[2 * k] = (float)t64[2 * k];
+                t32[2 * k + 1] = (float)t64[2 * k + 1];
+            }
+            void *p64 = nullptr, *p32 = nullptr;
+            if ((e = cudaMalloc(&p64, sizeof(double) * 2 * c.P)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+            h->tw64[c.P] = p64;
+            if ((e = cudaMalloc(&p32, sizeof(float) * 2 * c.P)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+            h->tw32[c.P] = p32;
+            cudaMemcpy(p64, t64.data(), sizeof(double) * 2 * c.P, cudaMemcpyHostToDevice);
+            cudaMemcpy(p32, t32.data(), sizeof(float) * 2 * c.P, cudaMemcpyHostToDevice);
+        }
+    }
+    if ((e = cudaMallocHost(&h->reps_ring, sizeof(Replica) * B * nd_handle::kSlots)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocHost");
+    h->reps_h = h->reps_ring;
+    for (int k = 0; k < nd_handle::kSlots; ++k)
+        if ((e = cudaEventCreateWithFlags(&h->slot_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaMalloc(&h->reps_d, sizeof(Replica) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->red_d, sizeof(double) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&h->red_h, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMalloc(&h->aux_d, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->aux_i, sizeof(int) * 2 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->acc, h->elt * h->state_elems)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    bool any_global = false, any_global64 = false;
+    for (auto &c : h->classes) { any_global |= !c.fused_main; any_global64 |= !c.fused_fp64; }
+    if (any_global || any_global64) {
+        if ((e = cudaMalloc(&h->spec, sizeof(double) * 2 * h->spec_words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    }
+    if (any_global && (e = cudaMalloc(&h->ms, h->elt * h->state_elems)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if (h->prec == ND_FP32 && (e = cudaMalloc((void **)&h->y64, sizeof(double) * h->state_elems)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    if (any_global64 && (e = cudaMalloc((void **)&h->ms64, sizeof(double) * h->state_elems)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+    for (int d = 0; d < n_disks; ++d) {
+        DiskInfo &di = h->disks[d];
+        const size_t kh = (size_t)(di.P / 2 + 1) * (di.P / 2 + 1) * 4;
+        if ((e = cudaMalloc(&di.mask_d, di.mask.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice);
+        if ((e = cudaMalloc(&di.ghat64, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMalloc(&di.ghat32, sizeof(float) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    }
+    for (int d = 0; d < n_disks; ++d) {
+        rc = nd_set_green_tensor(h, d, nullptr);
+        if (rc) { std::string m = g_err; nd_destroy(h); return fail(rc, m); }
+    }
+    *out = h;
+    g_err.clear();
+    return ND_OK;
+}
+
+void nd_destroy(nd_handle *h)
+{
+    if (!h) return;
+    for (auto &d : h->disks) { cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); }
+    for (auto &c : h->classes) cudaFree(c.work_d);
+    for (auto &kv : h->tw64) cudaFree(kv.second);
+    for (auto &kv : h->tw32) cudaFree(kv.second);
+    for (int k = 0; k < nd_handle::kSlots; ++k)
+        if (h->slot_ev[k]) { cudaEventSynchronize(h->slot_ev[k]); cudaEventDestroy(h->slot_ev[k]); }
+    cudaFreeHost(h->reps_ring);
+    cudaFree(h->reps_d);
+    cudaFree(h->red_d);
+    cudaFreeHost(h->red_h);
+    cudaFree(h->aux_d);
+    cudaFree(h->aux_i);
+    cudaFree(h->acc);
+    cudaFree(h->ms);
+    cudaFree(h->spec);
+    cudaFree(h->stage_in);
+    cudaFree(h->stage_out);
+    cudaFree(h->y64);
+    cudaFree(h->ms64);
+    delete h;
+}
+
+int nd_get_info(const nd_handle *h, int *n_replicas, long long *state_elems)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (n_replicas) *n_replicas = (int)h->rep_disk.size();
+    if (state_elems) *state_elems = h->state_elems;
+    return ND_OK;
+}
+
+int nd_replica_layout(const nd_handle *h, int r, int *D, int *Dpad, int *P, long long *offset, int *n_cells)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (r < 0 || r >= (int)h->rep_disk.size()) return fail(ND_ERR_ARG, "replica index out of range");
+    const DiskInfo &d = h->disks[h->rep_disk[r]];
+    if (D) *D = d.D;
+    if (Dpad) *Dpad = d.Dpad;
+    if (P) *P = d.P;
+    if (offset) *offset = h->rep_off[r];
+    if (n_cells) *n_cells = d.C;
+    return ND_OK;
+}
+
+int nd_disk_mask(const nd_handle *h, int d, unsigned char *mask_out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (d < 0 || d >= (int)h->disks.size() || !mask_out) return fail(ND_ERR_ARG, "bad disk index or output");
+    memcpy(mask_out, h->disks[d].mask.data(), h->disks[d].mask.size());
+    return ND_OK;
+}
+
+int nd_units(const nd_handle *h, int d, double out[8])
+{
+    if (int rc = check_handle(h)) return rc;
+    if (d < 0 || d >= (int)h->disks.size() || !out) return fail(ND_ERR_ARG, "bad disk index or output");
+    const DiskInfo &di = h->disks[d];
+    out[0] = di.lambda; out[1] = di.cfac; out[2] = di.B0; out[3] = di.t0;
+    out[4] = di.J; out[5] = di.Nx; out[6] = di.Nz; out[7] = di.C;
+    return ND_OK;
+}
+
+int nd_set_green_tensor(nd_handle *h, int d, const double *Gq)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (d < 0 || d >= (int)h->disks.size()) return fail(ND_ERR_ARG, "bad disk index");
+    DiskInfo &di = h->disks[d];
+    double *work = nullptr, *gq = nullptr;
+    ND_CUDA(cudaMalloc(&work, sizeof(double) * build_ghat_work_doubles(di.P, di.D)));
+    if (Gq) {
+        if (cudaMalloc(&gq, sizeof(double) * 4 * di.D * di.D) != cudaSuccess) {
+            cudaFree(work);
+            return fail(ND_ERR_CUDA, "cudaMalloc");
+        }
+        cudaMemcpy(gq, Gq, sizeof(double) * 4 * di.D * di.D, cudaMemcpyDefault);
+    }
+    cudaError_t e = build_ghat(di.P, di.D, di.desc.L / di.desc.a, di.Nx, di.Nz, di.cfac, gq, di.ghat64, di.ghat32, work, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(work);
+    cudaFree(gq);
+    if (e != cudaSuccess) return fail(ND_ERR_CUDA, std::string("spectral kernel build: ") + cudaGetErrorString(e));
+    return ND_OK;
+}
+
+int nd_set_damping(nd_handle *h, const double *alpha)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!alpha) return fail(ND_ERR_ARG, "null alpha");
+    for (size_t r = 0; r < h->alpha.size(); ++r) h->alpha[r] = alpha[r];
+    return ND_OK;
+}
+
+int nd_effective_field(nd_handle *h, const void *m, void *b, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr, *bd = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    if (!b) return fail(ND_ERR_ARG, "null output");
+    if (int rc = stage_in(h, b, &bd, false, st, &h->stage_out)) return rc;
+    ND_CUDA(cudaMemsetAsync(bd, 0, (size_t)h->state_elems * h->elt, st));
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    if (int rc = run_mode(h, M_FIELD, false, md, bd, 1, st)) return rc;
+    return stage_out(h, b, bd, st);
+}
+
+int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!E_out) return fail(ND_ERR_ARG, "null E_out");
+    if (dEdL_out) return fail(ND_ERR_ARG, "dEdL_out is reserved and must be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    const int B = (int)h->rep_disk.size();
+    void *y64 = md;
+    if (h->prec == ND_FP32) {
+        ND_CUDA(launch_convert(ND_PREC_FP64, md, h->y64, (size_t)h->state_elems, st));
+        y64 = h->y64;
+    }
+    fill_reps(h, true, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    ND_CUDA(cudaMemsetAsync(h->red_d, 0, sizeof(double) * B, st));
+    if (int rc = run_mode(h, M_ENERGY, true, y64, nullptr, 1, st)) return rc;
+    ND_CUDA(cudaMemcpyAsync(h->red_h, h->red_d, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < B; ++r) E_out[r] = h->red_h[r];
+    return ND_OK;
+}
+
+int nd_step_rk4(nd_handle *h, void *m, long long n_steps, double dt_seconds, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (n_steps < 0) return fail(ND_ERR_ARG, "negative n_steps");
+    if (!(dt_seconds > 0)) return fail(ND_ERR_ARG, "dt must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    if (n_steps > 0) {
+        fill_reps(h, h->prec == ND_FP64, dt_seconds, nullptr, nullptr, 0);
+        upload_reps(h, st);
+        if (int rc = run_mode(h, M_RK4, false, md, nullptr, n_steps, st)) return rc;
+    }
+    return stage_out(h, m, md, st);
+}
+
+int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, const double *T_kelvin,
+                 const unsigned long long *seed, unsigned long long step0, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (n_steps < 0) return fail(ND_ERR_ARG, "negative n_steps");
+    if (!(dt_seconds > 0)) return fail(ND_ERR_ARG, "dt must be positive");
+    if (!T_kelvin || !seed) return fail(ND_ERR_ARG, "T_kelvin and seed are required");
+    for (size_t r = 0; r < h->rep_disk.size(); ++r)
+        if (!(T_kelvin[r] >= 0)) return fail(ND_ERR_ARG, "temperatures must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    if (n_steps > 0) {
+        fill_reps(h, h->prec == ND_FP64, dt_seconds, T_kelvin, seed, step0);
+        upload_reps(h, st);
+        if (int rc = run_mode(h, M_HEUN, false, md, nullptr, n_steps, st)) return rc;
+    }
+    return stage_out(h, m, md, st);
+}
+
+int nd_init_vortex(nd_handle *h, void *m, const double *X0, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!X0) return fail(ND_ERR_ARG, "null X0");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, false, st, &h->stage_in)) return rc;
+    const int B = (int)h->rep_disk.size();
+    std::vector<double> xc(2 * B);
+    std::vector<int> pc(2 * B);
+    for (int r = 0; r < B; ++r) {
+        const DiskInfo &d = h->disks[h->rep_disk[r]];
+        xc[2 * r] = X0[2 * r] / d.desc.a;
+        xc[2 * r + 1] = X0[2 * r + 1] / d.desc.a;
+        pc[2 * r] = d.desc.polarity >= 0 ? 1 : -1;
+        pc[2 * r + 1] = d.desc.chirality >= 0 ? 1 : -1;
+    }
+    ND_CUDA(cudaMemcpyAsync(h->aux_d, xc.data(), sizeof(double) * 2 * B, cudaMemcpyHostToDevice, st));
+    ND_CUDA(cudaMemcpyAsync(h->aux_i, pc.data(), sizeof(int) * 2 * B, cudaMemcpyHostToDevice, st));
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    ND_CUDA(cudaMemsetAsync(md, 0, (size_t)h->state_elems * h->elt, st));
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        ND_CUDA(launch_init_vortex(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d,
+                                   (int)c.reps.size(), c.maxD, md, h->aux_d, h->aux_i, d.lambda / d.desc.a, st));
+    }
+    ND_CUDA(cudaStreamSynchronize(st));   // the host arrays above go out of scope
+    return stage_out(h, m, md, st);
+}
+
+int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!Xc_out) return fail(ND_ERR_ARG, "null Xc_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    const int B = (int)h->rep_disk.size();
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        for (int r : c.reps)
+            if (h->disks[h->rep_disk[r]].lambda / h->disks[h->rep_disk[r]].desc.a != d.lambda / d.desc.a)
+                return fail(ND_ERR_ARG, "vortex_core: disks of one size class must share lambda_ex / a");
+        const double rcut = 4.0 * d.lambda / d.desc.a;
+        ND_CUDA(launch_vortex_core(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d,
+                                   (int)c.reps.size(), md, rcut * rcut, h->aux_d, st));
+    }
+    ND_CUDA(cudaMemcpyAsync(h->red_h, h->aux_d, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    int rc = ND_OK;
+    for (int r = 0; r < B; ++r) {
+        const double a = h->disks[h->rep_disk[r]].desc.a;
+        const bool none = h->red_h[4 * r + 2] != 0.0;
+        Xc_out[2 * r] = none ? 0.0 : h->red_h[4 * r] * a;
+        Xc_out[2 * r + 1] = none ? 0.0 : h->red_h[4 * r + 1] * a;
+        if (status) status[r] = none ? ND_ERR_NO_VORTEX : ND_OK;
+        if (none) rc = ND_ERR_NO_VORTEX;
+    }
+    if (rc) g_err = "no vortex found in at least one replica";
+    return rc;
+}
+
+int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(ND_ERR_ARG, "null out");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    const int B = (int)h->rep_disk.size();
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    for (auto &c : h->classes)
+        ND_CUDA(launch_mean_m(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d, (int)c.reps.size(),
+                              md, h->aux_d, st));
+    ND_CUDA(cudaMemcpyAsync(h->red_h, h->aux_d, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < 3 * B; ++i) out[i] = h->red_h[i];
+    return ND_OK;
+}
+
+}  // extern "C"

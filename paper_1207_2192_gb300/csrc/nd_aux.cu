@@ -1,0 +1,336 @@
+// nd_aux.cu -- once-per-geometry spectral kernel build and the small
+// per-replica kernels: analytic vortex profile, vortex-core estimator, <m>,
+// precision conversion and finiteness check.
+#include <math.h>
+
+#include "nd_common.cuh"
+#include "nd_kernels.h"
+
+namespace nd {
+
+// --------------------------------------------------- spectral kernel build
+
+// a^2 G at cell displacement (dx, dy) >= 0, lengths in units of a (Section
+// II.B): G_zz = -l/(2 pi r s (s+r)), G_xx = l/(2 pi r^4) (x^2/s - y^2/(s+r)),
+// G_xy = l/(2 pi r^4) (2s+r)/(s+r) x y/s, s = sqrt(r^2 + l^2); the origin holds
+// the cell self terms -Nx, -Nx, 0, -Nz.
+__global__ void k_green_quarter(int D, double l, double Nx, double Nz, double *Gq)
+{
+    const int n = D * D;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int dy = i / D, dx = i - dy * D;
+        double xx, yy, xy, zz;
+        if (dx == 0 && dy == 0) {
+            xx = -Nx; yy = -Nx; xy = 0.0; zz = -Nz;
+        } else {
+            const double x = dx, y = dy, r2 = x * x + y * y, r = sqrt(r2), s = sqrt(r2 + l * l);
+            const double pre = l / (2.0 * M_PI * r2 * r2);
+            xx = pre * (x * x / s - y * y / (s + r));
+            yy = pre * (y * y / s - x * x / (s + r));
+            xy = pre * ((2.0 * s + r) / (s + r)) * (x * y / s);
+            zz = -l / (2.0 * M_PI * r * s * (s + r));
+        }
+        Gq[i] = xx; Gq[n + i] = yy; Gq[2 * n + i] = xy; Gq[3 * n + i] = zz;
+    }
+}
+
+__global__ void k_trig_table(int P, double *cs)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * k / P, &s, &c);
+        cs[2 * k] = c; cs[2 * k + 1] = s;
+    }
+}
+
+// Pass 1 over dx: T1[c][dy][kx] = sum_dx w(dx) Gq[c][dy][dx] f_c(2 pi kx dx / P),
+// f = cos for the even components (xx, yy, zz), sin for the odd one (xy),
+// w = 1 at dx = 0 and 2 otherwise (the two signs of dx folded together).
+__global__ void k_ghat_pass1(int P, int D, const double *Gq, const double *cs, double *T1)
+{
+    const int KH = P / 2 + 1, n = 4 * D * KH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int kx = i % KH, dy = (i / KH) % D, c = i / (KH * D);
+        const double *g = Gq + (size_t)c * D * D + (size_t)dy * D;
+        double acc = 0.0;
+        for (int dx = 0; dx < D; ++dx) {
+            const int k = (int)(((long long)kx * dx) % P);
+            const double f = (c == 2) ? cs[2 * k + 1] : cs[2 * k];
+            acc += (dx == 0 ? 1.0 : 2.0) * g[dx] * f;
+        }
+        T1[i] = acc;
+    }
+}
+
+// Pass 2 over dy and final assembly into [kx][ky][4]:
+//   Ghat_c = s_c sum_dy w(dy) T1[c][dy][kx] f_c(2 pi ky dy / P), s_xy = -1,
+//   diagonal: (c Ghat + 2 cos(2 pi kx/P) + 2 cos(2 pi ky/P)) / P^2 (exchange folded in),
+//   xy:       c Ghat_xy / P^2.
+__global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const double *cs, double *G64, float *G32)
+{
+    const int KH = P / 2 + 1, n = KH * KH;
+    const double inv = 1.0 / ((double)P * (double)P);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int kx = i / KH, ky = i % KH;
+        double v[4];
+        for (int c = 0; c < 4; ++c) {
+            const double *t1 = T1 + (size_t)c * D * KH + kx;
+            double acc = 0.0;
+            for (int dy = 0; dy < D; ++dy) {
+                const int k = (int)(((long long)ky * dy) % P);
+                const double f = (c == 2) ? cs[2 * k + 1] : cs[2 * k];
+                acc += (dy == 0 ? 1.0 : 2.0) * t1[(size_t)dy * KH] * f;
+            }
+            v[c] = (c == 2) ? -acc : acc;
+        }
+        const double kex = 2.0 * cs[2 * kx] + 2.0 * cs[2 * ky];
+        const double o[4] = {(cfac * v[0] + kex) * inv, (cfac * v[1] + kex) * inv, cfac * v[2] * inv,
+                             (cfac * v[3] + kex) * inv};
+        for (int c = 0; c < 4; ++c) {
+            G64[(size_t)i * 4 + c] = o[c];
+            if (G32) G32[(size_t)i * 4 + c] = (float)o[c];
+        }
+    }
+}
+
+size_t build_ghat_work_doubles(int P, int D) { return (size_t)4 * D * D + (size_t)4 * D * (P / 2 + 1) + 2 * (size_t)P; }
+
+cudaError_t build_ghat(int P, int D, double l, double Nx, double Nz, double cfac, const double *Gq_dev, double *G64,
+                       float *G32, double *work, cudaStream_t st)
+{
+    double *Gq = work, *T1 = Gq + (size_t)4 * D * D, *cs = T1 + (size_t)4 * D * (P / 2 + 1);
+    if (Gq_dev) {
+        cudaError_t e = cudaMemcpyAsync(Gq, Gq_dev, sizeof(double) * 4 * D * D, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_green_quarter<<<(D * D + 255) / 256, 256, 0, st>>>(D, l, Nx, Nz, Gq);
+    }
+    k_trig_table<<<(P + 255) / 256, 256, 0, st>>>(P, cs);
+    const int KH = P / 2 + 1;
+    k_ghat_pass1<<<(4 * D * KH + 255) / 256, 256, 0, st>>>(P, D, Gq, cs, T1);
+    k_ghat_pass2<<<(KH * KH + 127) / 128, 128, 0, st>>>(P, D, cfac, T1, cs, G64, G32);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------- vortex profile
+
+// Planar q = +1 vortex at X0 (Section IV) with a seeded core:
+// phi = atan2(y - y0, x - x0) + chirality pi/2, m_z = polarity exp(-rho^2/lambda^2).
+template <typename T>
+__global__ void k_init_vortex(const Replica *reps, const int *work, T *ybase, const double *X0, const int *pc,
+                              double lam)
+{
+    const int ridx = work[blockIdx.y];
+    const Replica r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const long long cs = (long long)D * r.Dpad;
+    const double x0 = X0[2 * ridx], y0 = X0[2 * ridx + 1];
+    const int pol = pc[2 * ridx], chi = pc[2 * ridx + 1];
+    T *y = ybase + r.state_off;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < DD; cell += gridDim.x * blockDim.x) {
+        const int j = cell / D, i = cell - j * D;
+        const long long si = (long long)j * r.Dpad + i;
+        double mx = 0, my = 0, mz = 0;
+        if (r.mask[cell]) {
+            const double x = i - 0.5 * (D - 1), yy = j - 0.5 * (D - 1);
+            const double rho2 = (x - x0) * (x - x0) + (yy - y0) * (yy - y0);
+            mz = pol * exp(-rho2 / (lam * lam));
+            const double phi = atan2(yy - y0, x - x0) + chi * 0.5 * M_PI;
+            const double sp = sqrt(1.0 - mz * mz);
+            double sn, cn;
+            sincos(phi, &sn, &cn);
+            mx = sp * cn; my = sp * sn;
+        }
+        y[si] = (T)mx; y[cs + si] = (T)my; y[2 * cs + si] = (T)mz;
+    }
+    // cells of the padded columns stay untouched
+}
+
+cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, int nwork, int maxD, void *y,
+                               const double *X0, const int *pc, double lam, cudaStream_t st)
+{
+    dim3 g((maxD * maxD + 255) / 256, nwork);
+    if (prec == ND_PREC_FP64) k_init_vortex<double><<<g, 256, 0, st>>>(reps, work, (double *)y, X0, pc, lam);
+    else k_init_vortex<float><<<g, 256, 0, st>>>(reps, work, (float *)y, X0, pc, lam);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ vortex core
+
+// Core position estimator (Section IV), one CTA per replica.  The plaquette
+// windings and the m_z^2 corner sums are evaluated in double precision with
+// no fused multiply-adds, in the same order as the CPU reference, so both
+// take the same integer decisions from the same inputs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_vortex_core(const Replica *reps, const int *work, const T *ybase, double rc2,
+                                                     double *out)
+{
+    __shared__ double sw[256];
+    __shared__ int si_[256];
+    __shared__ double sx[3][8];
+    const int ridx = work[blockIdx.x];
+    const Replica r = reps[ridx];
+    const int D = r.D, tid = threadIdx.x;
+    const long long cs = (long long)D * r.Dpad;
+    const T *y = ybase + r.state_off;
+    auto at = [&](int cell, int c) -> double {
+        const int j = cell / D, i = cell - j * D;
+        return (double)y[c * cs + (long long)j * r.Dpad + i];
+    };
+    double bw = -1.0;
+    int bi = 0x7fffffff;
+    const int np = (D - 1) * (D - 1);
+    for (int p = tid; p < np; p += 256) {
+        const int j = p / (D - 1), i = p - j * (D - 1);
+        const int t = j * D + i;
+        if (!(r.mask[t] && r.mask[t + 1] && r.mask[t + D] && r.mask[t + D + 1])) continue;
+        const int c[4] = {t, t + 1, t + D + 1, t + D};
+        double s = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const int p0 = c[q], p1 = c[(q + 1) & 3];
+            const double ax = at(p0, 0), ay = at(p0, 1), bx = at(p1, 0), by = at(p1, 1);
+            const double cr = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
+            const double dt = __dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by));
+            s = __dadd_rn(s, atan2(cr, dt));
+        }
+        if (llround(s / (2.0 * M_PI)) != 1) continue;
+        const double z0 = at(t, 2), z1 = at(t + 1, 2), z2 = at(t + D, 2), z3 = at(t + D + 1, 2);
+        double w = __dmul_rn(z0, z0);
+        w = __dadd_rn(w, __dmul_rn(z1, z1));
+        w = __dadd_rn(w, __dmul_rn(z2, z2));
+        w = __dadd_rn(w, __dmul_rn(z3, z3));
+        if (w > bw || (w == bw && t < bi)) { bw = w; bi = t; }
+    }
+    sw[tid] = bw; si_[tid] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o) {
+            const double w2 = sw[tid + o];
+            const int i2 = si_[tid + o];
+            if (w2 > sw[tid] || (w2 == sw[tid] && i2 < si_[tid])) { sw[tid] = w2; si_[tid] = i2; }
+        }
+        __syncthreads();
+    }
+    const int best = si_[0];
+    const bool found = sw[0] >= 0.0 && best != 0x7fffffff;
+    double cx = 0, cy = 0;
+    if (found) {
+        const int bj = best / D, bii = best - bj * D;
+        cx = bii + 0.5 - 0.5 * (D - 1);
+        cy = bj + 0.5 - 0.5 * (D - 1);
+    }
+    double a0 = 0, a1 = 0, a2 = 0;
+    if (found) {
+        for (int cell = tid; cell < D * D; cell += 256) {
+            if (!r.mask[cell]) continue;
+            const int j = cell / D, i = cell - j * D;
+            const double x = i - 0.5 * (D - 1), yy = j - 0.5 * (D - 1);
+            const double dx = x - cx, dy = yy - cy;
+            if (dx * dx + dy * dy >= rc2) continue;
+            const double z = at(cell, 2), w = z * z;
+            a0 += w; a1 += w * x; a2 += w * yy;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((tid & 31) == 0) { sx[0][tid >> 5] = a0; sx[1][tid >> 5] = a1; sx[2][tid >> 5] = a2; }
+    __syncthreads();
+    if (tid == 0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < 8; ++w) { s0 += sx[0][w]; s1 += sx[1][w]; s2 += sx[2][w]; }
+        double *o = out + 4 * ridx;
+        if (found && s0 > 0.0) { o[0] = s1 / s0; o[1] = s2 / s0; o[2] = 0.0; }
+        else { o[0] = 0.0; o[1] = 0.0; o[2] = 1.0; }
+        o[3] = found ? (double)best : -1.0;
+    }
+}
+
+cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, const void *y, double rc2,
+                               double *out, cudaStream_t st)
+{
+    if (prec == ND_PREC_FP64) k_vortex_core<double><<<nwork, 256, 0, st>>>(reps, work, (const double *)y, rc2, out);
+    else k_vortex_core<float><<<nwork, 256, 0, st>>>(reps, work, (const float *)y, rc2, out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- <m>
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mean_m(const Replica *reps, const int *work, const T *ybase, double *out)
+{
+    __shared__ double sx[4][8];
+    const int ridx = work[blockIdx.x];
+    const Replica r = reps[ridx];
+    const int D = r.D, tid = threadIdx.x;
+    const long long cs = (long long)D * r.Dpad;
+    const T *y = ybase + r.state_off;
+    double a0 = 0, a1 = 0, a2 = 0, n = 0;
+    for (int cell = tid; cell < D * D; cell += 256) {
+        if (!r.mask[cell]) continue;
+        const int j = cell / D, i = cell - j * D;
+        const long long si = (long long)j * r.Dpad + i;
+        a0 += (double)y[si]; a1 += (double)y[cs + si]; a2 += (double)y[2 * cs + si]; n += 1.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if ((tid & 31) == 0) { sx[0][tid >> 5] = a0; sx[1][tid >> 5] = a1; sx[2][tid >> 5] = a2; sx[3][tid >> 5] = n; }
+    __syncthreads();
+    if (tid == 0) {
+        double s[4] = {0, 0, 0, 0};
+        for (int w = 0; w < 8; ++w) for (int c = 0; c < 4; ++c) s[c] += sx[c][w];
+        for (int c = 0; c < 3; ++c) out[3 * ridx + c] = s[c] / s[3];
+    }
+}
+
+cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y, double *out,
+                          cudaStream_t st)
+{
+    if (prec == ND_PREC_FP64) k_mean_m<double><<<nwork, 256, 0, st>>>(reps, work, (const double *)y, out);
+    else k_mean_m<float><<<nwork, 256, 0, st>>>(reps, work, (const float *)y, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- conversion, checks
+
+template <typename S, typename D_>
+__global__ void k_convert(const S *src, D_ *dst, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (D_)src[i];
+}
+
+cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st)
+{
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (n == 0) return cudaSuccess;
+    if (to_prec == ND_PREC_FP64) k_convert<float, double><<<blocks, 256, 0, st>>>((const float *)src, (double *)dst, n);
+    else k_convert<double, float><<<blocks, 256, 0, st>>>((const double *)src, (float *)dst, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_check_finite(const T *y, size_t n, unsigned *flag)
+{
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        bad |= !isfinite((double)y[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, ND_DEV_NAN);
+}
+
+cudaError_t launch_check_finite(int prec, const void *y, size_t n, unsigned *flag, cudaStream_t st)
+{
+    const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    if (n == 0) return cudaSuccess;
+    if (prec == ND_PREC_FP64) k_check_finite<double><<<blocks, 256, 0, st>>>((const double *)y, n, flag);
+    else k_check_finite<float><<<blocks, 256, 0, st>>>((const float *)y, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace nd

@@ -1,0 +1,102 @@
+// nd_common.cuh -- shared device helpers of the GB300 thin-nanodisk library:
+// complex arithmetic, constant-bank twiddles, the Philox4x32-10 noise stream
+// and the per-replica work descriptors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nd {
+
+template <typename T> struct cplx { T x, y; };
+template <typename T> struct vec3 { T x, y, z; };
+
+template <typename T> __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b)  // a * conj(b)
+{
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T> __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.x, -a.y}; }
+template <typename T> __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T drsqrt(T x);
+template <> __device__ __forceinline__ float drsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double drsqrt<double>(double x) { return 1.0 / sqrt(x); }
+
+// ------------------------------------------------------------- Philox noise
+
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of the
+// 32x32->64 multiply-xor round with the published multipliers and Weyl key
+// increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Three standard normals of one cell and one time step: key = seed words,
+// counter = (cell, step low, step high, 0); Box-Muller on the pairs (r0, r1)
+// and (r2, r3) with u = (r + 1) 2^-32 and angle 2 pi r 2^-32.
+template <typename T> __device__ __forceinline__ vec3<T> thermal_normals(uint64_t seed, uint32_t cell, uint64_t step);
+
+template <> __device__ __forceinline__ vec3<float> thermal_normals<float>(uint64_t seed, uint32_t cell, uint64_t step)
+{
+    uint4 r = philox4x32_10(make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u), (uint32_t)seed,
+                            (uint32_t)(seed >> 32));
+    const float s32 = 2.3283064365386963e-10f;
+    // (r + 1) 2^-32 formed in double then rounded once, so u > 0 for every r
+    float u0 = (float)(((double)r.x + 1.0) * 2.3283064365386963e-10), u2 = (float)(((double)r.z + 1.0) * 2.3283064365386963e-10);
+    float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * (float)r.y * s32, &s1, &c1);
+    sincospif(2.0f * (float)r.w * s32, &s3, &c3);
+    return {ra * c1, ra * s1, rb * c3};
+}
+
+template <> __device__ __forceinline__ vec3<double> thermal_normals<double>(uint64_t seed, uint32_t cell, uint64_t step)
+{
+    uint4 r = philox4x32_10(make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u), (uint32_t)seed,
+                            (uint32_t)(seed >> 32));
+    const double s32 = 2.3283064365386963e-10;
+    double u0 = ((double)r.x + 1.0) * s32, u2 = ((double)r.z + 1.0) * s32;
+    double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * (double)r.y * s32, &s1, &c1);
+    sincospi(2.0 * (double)r.w * s32, &s3, &c3);
+    return {ra * c1, ra * s1, rb * c3};
+}
+
+// ------------------------------------------------------------ descriptors
+
+// One replica (one disk state) as the kernels see it.
+struct Replica {
+    int D, Dpad;                 // grid side and padded row length of the state
+    int disk;                    // disk index (geometry)
+    int flags;                   // bit 0: thermal noise on
+    long long state_off;         // element offset of this replica's [3][D][Dpad] block
+    long long spec_off;          // complex-element offset of its [3][D][RS] spectrum (global path)
+    const void *Ghat;            // [P/2+1 (kx)][P/2+1 (ky)][4] spectral kernel, incl. exchange and 1/P^2
+    const unsigned char *mask;   // [D][D]
+    double chext[3];             // (a^2/lambda^2) h_ext
+    double alpha, dtau, sigma;   // damping, dimensionless step, noise amplitude
+    unsigned long long seed, step0;
+};
+
+// Status word written by kernels (bit flags), read by the host after a sync.
+enum : unsigned { ND_DEV_NAN = 1u, ND_DEV_TIMEOUT = 2u };
+
+}  // namespace nd

@@ -1,0 +1,47 @@
+// nd_dispatch.cu -- precision dispatch between the instantiation units.
+#include "nd_kernels.h"
+
+namespace nd {
+
+cudaError_t upload_tw_fused_f32(const double *, const double *);
+cudaError_t upload_tw_fused_f64(const double *, const double *);
+cudaError_t upload_tw_glob_f32(const double *, const double *);
+cudaError_t upload_tw_glob_f64(const double *, const double *);
+size_t fused_smem_f32(int P, int D, int Dpad);
+size_t fused_smem_f64(int P, int D, int Dpad);
+cudaError_t launch_fused_f32(int P, const LaunchArgs &a);
+cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
+cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
+cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD);
+
+cudaError_t upload_twiddle_constants(const double *re, const double *im)
+{
+    cudaError_t e;
+    if ((e = upload_tw_fused_f32(re, im)) != cudaSuccess) return e;
+    if ((e = upload_tw_fused_f64(re, im)) != cudaSuccess) return e;
+    if ((e = upload_tw_glob_f32(re, im)) != cudaSuccess) return e;
+    return upload_tw_glob_f64(re, im);
+}
+
+size_t fused_smem(int P, int prec, int D, int Dpad)
+{
+    return prec == ND_PREC_FP64 ? fused_smem_f64(P, D, Dpad) : fused_smem_f32(P, D, Dpad);
+}
+
+cudaError_t launch_fused(int P, int prec, const LaunchArgs &a)
+{
+    return prec == ND_PREC_FP64 ? launch_fused_f64(P, a) : launch_fused_f32(P, a);
+}
+
+cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD)
+{
+    return prec == ND_PREC_FP64 ? launch_global_f64(P, a, maxD) : launch_global_f32(P, a, maxD);
+}
+
+size_t spec_words(int P, int D)
+{
+    const int RS = (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);   // matches SpecGeom<P>::RS
+    return (size_t)3 * D * RS;
+}
+
+}  // namespace nd

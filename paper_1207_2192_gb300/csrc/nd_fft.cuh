@@ -1,0 +1,171 @@
+// nd_fft.cuh -- register-resident FFTs for the padded grid sizes P = 16..1024.
+//
+// A length-P transform runs on a group of G threads (G consecutive lanes of one
+// warp), each holding R1 = P/G points in registers.  Thread t owns the points
+// with index = t (mod G) in natural order, both on input and on output:
+//   register o of thread t  <->  element t + G*o.
+// The transform is the two-pass ("four-step") split P = R1 x G:
+//   1. an R1-point DFT in registers over the strided points of each thread,
+//   2. a twiddle exp(-+2 pi i t k1 / P) read from a small shared table,
+//   3. one transpose through a padded per-group shared scratch area,
+//   4. R1/G G-point DFTs in registers,
+// so every point crosses shared memory exactly once.  Register DFTs are
+// radix-2 decimation in time with compile-time twiddles from the constant bank.
+#pragma once
+#include "nd_common.cuh"
+
+namespace nd {
+
+// 32nd roots of unity exp(-2 pi i k / 32), k = 0..31, in the constant bank.
+// Each translation unit that includes this header owns a copy, filled by its
+// own upload hook (ND_DEFINE_TWIDDLE_UPLOAD).  Indices are compile-time
+// constants in the register DFTs, so each use becomes a constant-bank operand.
+static __constant__ float2 c_w32f[32];
+static __constant__ double2 c_w32d[32];
+
+template <typename T> __device__ __forceinline__ cplx<T> w32(int k);
+template <> __device__ __forceinline__ cplx<float> w32<float>(int k) { float2 v = c_w32f[k]; return {v.x, v.y}; }
+template <> __device__ __forceinline__ cplx<double> w32<double>(int k) { double2 v = c_w32d[k]; return {v.x, v.y}; }
+
+#define ND_DEFINE_TWIDDLE_UPLOAD(name)                                                  \
+    cudaError_t name(const double *re, const double *im)                                \
+    {                                                                                   \
+        float2 f[32];                                                                   \
+        double2 d[32];                                                                  \
+        for (int k = 0; k < 32; ++k) {                                                  \
+            f[k] = make_float2((float)re[k], (float)im[k]);                             \
+            d[k] = make_double2(re[k], im[k]);                                          \
+        }                                                                               \
+        cudaError_t e = cudaMemcpyToSymbol(c_w32f, f, sizeof(f));                        \
+        if (e != cudaSuccess) return e;                                                 \
+        return cudaMemcpyToSymbol(c_w32d, d, sizeof(d));                                \
+    }
+
+template <int P> struct FFTShape;
+template <> struct FFTShape<16> { static constexpr int G = 4; };
+template <> struct FFTShape<32> { static constexpr int G = 4; };
+template <> struct FFTShape<64> { static constexpr int G = 8; };
+template <> struct FFTShape<128> { static constexpr int G = 8; };
+template <> struct FFTShape<256> { static constexpr int G = 16; };
+template <> struct FFTShape<512> { static constexpr int G = 16; };
+template <> struct FFTShape<1024> { static constexpr int G = 32; };
+
+template <int P> struct FFTGeom {
+    static constexpr int G = FFTShape<P>::G;
+    static constexpr int R1 = P / G;
+    static_assert(R1 % G == 0, "R1 must be a multiple of G");
+    static constexpr int R2 = R1 / G;  // G-point DFTs per thread in pass 2
+    // per-group scratch: R1 rows of G+1 (padding breaks the stride-G conflicts),
+    // rounded so consecutive groups start 8 complex words apart modulo 16
+    static constexpr int SROW = G + 1;
+    static constexpr int SRAW = R1 * SROW;
+    static constexpr int SCRATCH = SRAW + ((8 - SRAW % 16) + 16) % 16;
+    static constexpr int GROUPS_PER_WARP = 32 / G;
+};
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+__host__ __device__ constexpr int bitrev(int i, int bits)
+{
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// b * w^k for the N-th root w = exp(DIR 2 pi i / N) (DIR = -1 forward), with
+// the trivial factors 1 and -+i special-cased; k and N are constants after the
+// register DFT loops are unrolled, so the branches fold away.
+template <int DIR, typename T>
+__device__ __forceinline__ cplx<T> twid(cplx<T> b, int k, int N)
+{
+    if (k == 0) return b;
+    if (4 * k == N) {  // exp(DIR i pi / 2) = DIR * i
+        return DIR < 0 ? cplx<T>{b.y, -b.x} : cplx<T>{-b.y, b.x};
+    }
+    cplx<T> w = w32<T>(k * (32 / N));
+    return DIR < 0 ? cmul(b, w) : cmulc(b, w);
+}
+
+// In-register N-point DFT (N = 2..32), natural order in and out:
+// v[k] <- sum_n v[n] exp(DIR 2 pi i n k / N).
+template <int N, int DIR, typename T>
+__device__ __forceinline__ void dft_reg(cplx<T> *v)
+{
+    constexpr int B = ilog2c(N);
+    cplx<T> u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[bitrev(i, B)] = v[i];
+#pragma unroll
+    for (int half = 1; half < N; half *= 2) {
+#pragma unroll
+        for (int g = 0; g < N; g += 2 * half) {
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                cplx<T> a = u[g + j];
+                cplx<T> b = twid<DIR>(u[g + j + half], j, 2 * half);
+                u[g + j] = cadd(a, b);
+                u[g + j + half] = csub(a, b);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = u[i];
+}
+
+// Full P-point transform on a group of G threads.
+//   v      : the thread's R1 points, element t + G*o in v[o]; replaced by the
+//            transform in the same layout
+//   t      : index of the thread in its group (0..G-1)
+//   scr    : this group's private shared scratch, FFTGeom<P>::SCRATCH words
+//   tw     : shared twiddle table [R1][G], tw[k1*G + t] = exp(-2 pi i t k1 / P)
+//   gmask  : lane mask of the group (for __syncwarp)
+template <int P, int DIR, typename T>
+__device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, R2 = Gm::R2, SROW = Gm::SROW;
+    dft_reg<R1, DIR>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+        cplx<T> w = tw[k1 * G + t];
+        v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) scr[k1 * SROW + t] = v[k1];
+    __syncwarp(gmask);
+#pragma unroll
+    for (int i = 0; i < R2; ++i)
+#pragma unroll
+        for (int s = 0; s < G; ++s) v[i * G + s] = scr[(t + G * i) * SROW + s];
+    __syncwarp(gmask);
+#pragma unroll
+    for (int i = 0; i < R2; ++i) dft_reg<G, DIR>(v + i * G);
+    // v[i*G + k2] holds X[t + G*i + R1*k2] = X[t + G*(i + R2*k2)]: reorder to o = i + R2*k2
+    cplx<T> o_[R1];
+#pragma unroll
+    for (int i = 0; i < R2; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) o_[i + R2 * k2] = v[i * G + k2];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) v[o] = o_[o];
+}
+
+// Mirror values: for each register o (element k = t + G*o) return the value
+// the group holds at element (P - k) mod P.  Those live on lane (G - t) mod G,
+// register (R1 - 1 - o) for t > 0 and (R1 - o) mod R1 for t = 0.
+template <int P, typename T>
+__device__ __forceinline__ void mirror_group(const cplx<T> *v, cplx<T> *w, int t, int lane)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1;
+    int src = (lane - t) + ((G - t) & (G - 1));
+    cplx<T> r[R1];
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+        r[q].x = __shfl_sync(0xffffffffu, v[q].x, src);
+        r[q].y = __shfl_sync(0xffffffffu, v[q].y, src);
+    }
+#pragma unroll
+    for (int o = 0; o < R1; ++o) w[o] = (t == 0) ? r[(R1 - o) % R1] : r[R1 - 1 - o];
+}
+
+}  // namespace nd

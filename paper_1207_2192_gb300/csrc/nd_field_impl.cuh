@@ -1,0 +1,425 @@
+// nd_field_impl.cuh -- field evaluation and time stepping kernels (templates;
+// instantiated by nd_fused_f32.cu, nd_fused_f64.cu, nd_glob_f32.cu, nd_glob_f64.cu).
+//
+// Two drivers share the passes of nd_phases.cuh:
+//  * k_fused<P, T, MODE>: one CTA owns one replica for a whole launch.  The
+//    half spectrum, the stage magnetisation and the FFT scratch live in shared
+//    memory; a launch runs n_steps full time steps (RK4: four field
+//    evaluations per step, Heun: two) without touching the spectrum in HBM.
+//    Used when the CTA's shared-memory footprint fits (P <= 128 in FP32).
+//  * k_g_*: the same passes as separate grid-wide kernels with the spectrum
+//    in global memory, for the large padded grids (P = 256..1024) and FP64 at
+//    P = 128.
+// The LLG right-hand side, the RK4 combine, the stochastic Heun predictor and
+// corrector with Philox noise and the |m| = 1 renormalisation are fused into
+// the epilogue that consumes the inverse transform.
+#pragma once
+#include "nd_kernels.h"
+#include "nd_phases.cuh"
+
+namespace nd {
+
+// ------------------------------------------------------------- epilogue
+
+template <typename T> __device__ __forceinline__ vec3<T> v3(T x, T y, T z) { return {x, y, z}; }
+template <typename T> __device__ __forceinline__ vec3<T> cross3(vec3<T> a, vec3<T> b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ vec3<T> axpy3(T s, vec3<T> a, vec3<T> b)
+{
+    return {b.x + s * a.x, b.y + s * a.y, b.z + s * a.z};
+}
+template <typename T> __device__ __forceinline__ vec3<T> normalize3(vec3<T> v)
+{
+    T r = drsqrt<T>(v.x * v.x + v.y * v.y + v.z * v.z);
+    return {v.x * r, v.y * r, v.z * r};
+}
+// Landau-Lifshitz right-hand side m x b - alpha m x (m x b) (Section III.A).
+template <typename T> __device__ __forceinline__ vec3<T> llg_rhs(vec3<T> m, vec3<T> b, T alpha)
+{
+    vec3<T> p = cross3(m, b), q = cross3(m, p);
+    return {p.x - alpha * q.x, p.y - alpha * q.y, p.z - alpha * q.z};
+}
+// One Heun stage change m x [g - alpha m x g], g = b dtau + sigma w (Section III.C).
+template <typename T> __device__ __forceinline__ vec3<T> heun_dm(vec3<T> m, vec3<T> g, T alpha)
+{
+    vec3<T> p = cross3(m, g);
+    return cross3(m, vec3<T>{g.x - alpha * p.x, g.y - alpha * p.y, g.z - alpha * p.z});
+}
+
+template <typename T> struct V3Ptr {
+    T *p;
+    long long s;  // component stride
+    __device__ __forceinline__ vec3<T> ld(long long i) const { return {p[i], p[s + i], p[2 * s + i]}; }
+    __device__ __forceinline__ void st(long long i, vec3<T> v) const { p[i] = v.x; p[s + i] = v.y; p[2 * s + i] = v.z; }
+};
+
+// Per-cell epilogue of one field evaluation.
+//   ms  : stage magnetisation (read; overwritten with the next stage's input)
+//   yn  : state y_n (user buffer), acc : stage accumulator (scratch)
+//   b   : the full dimensionless induction b_i at this cell
+// Returns the cell's contribution to the reduced quantity (energy mode).
+template <typename T, int MODE>
+__device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long long si, long long mi, vec3<T> b,
+                                                V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
+                                                unsigned long long step)
+{
+    const T alpha = (T)r.alpha, dt = (T)r.dtau;
+    vec3<T> m = ms.ld(mi);
+    if (MODE == M_FIELD) {
+        out.st(si, b);
+        return 0.0;
+    } else if (MODE == M_ENERGY) {
+        // E/J = -sum_i m_i . (b'_i / 2 + c h_ext), b' = b - c h_ext  (Eq. Hmm)
+        double bx = (double)b.x - r.chext[0], by = (double)b.y - r.chext[1], bz = (double)b.z - r.chext[2];
+        return -((double)m.x * (0.5 * bx + r.chext[0]) + (double)m.y * (0.5 * by + r.chext[1]) +
+                 (double)m.z * (0.5 * bz + r.chext[2]));
+    } else if (MODE == M_RK4) {
+        vec3<T> k = llg_rhs(m, b, alpha);
+        if (stage == 0) {
+            acc.st(si, k);
+            ms.st(mi, axpy3(T(0.5) * dt, k, m));
+        } else if (stage < 3) {
+            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            acc.st(si, axpy3(T(2), k, a));
+            ms.st(mi, axpy3(stage == 1 ? T(0.5) * dt : dt, k, y));
+        } else {
+            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            vec3<T> s = {a.x + k.x, a.y + k.y, a.z + k.z};
+            vec3<T> yo = normalize3(axpy3(dt / T(6), s, y));
+            yn.st(si, yo);
+            ms.st(mi, yo);
+        }
+        return 0.0;
+    } else if (MODE == M_HEUN) {
+        const T sig = (T)r.sigma;
+        vec3<T> g = {b.x * dt, b.y * dt, b.z * dt};
+        if (r.flags & 1) {
+            vec3<T> w = thermal_normals<T>(r.seed, (uint32_t)cell, step);
+            g.x += sig * w.x; g.y += sig * w.y; g.z += sig * w.z;
+        }
+        vec3<T> d = heun_dm(m, g, alpha);
+        if (stage == 0) {
+            acc.st(si, d);
+            ms.st(mi, normalize3(vec3<T>{m.x + d.x, m.y + d.y, m.z + d.z}));
+        } else {
+            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            vec3<T> yo = normalize3(vec3<T>{y.x + T(0.5) * (a.x + d.x), y.y + T(0.5) * (a.y + d.y),
+                                            y.z + T(0.5) * (a.z + d.z)});
+            yn.st(si, yo);
+            ms.st(mi, yo);
+        }
+        return 0.0;
+    }
+    return 0.0;
+}
+
+template <int MODE> struct ModeStages { static constexpr int n = 1; };
+template <> struct ModeStages<M_RK4> { static constexpr int n = 4; };
+template <> struct ModeStages<M_HEUN> { static constexpr int n = 2; };
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------ fused path
+
+template <int P, typename T>
+__host__ __device__ __forceinline__ size_t fused_smem_bytes(int D, int Dpad, int nthreads)
+{
+    using Gm = FFTGeom<P>;
+    size_t tw = sizeof(cplx<T>) * Gm::R1 * Gm::G;
+    size_t spec = sizeof(cplx<T>) * 3 * (size_t)D * SpecGeom<P>::RS;
+    size_t scr = sizeof(cplx<T>) * (size_t)(nthreads / Gm::G) * Gm::SCRATCH;
+    size_t ms = sizeof(T) * 3 * (size_t)D * Dpad;
+    size_t red = sizeof(double) * 32;
+    return tw + spec + scr + ms + red;
+}
+
+template <int P, typename T, int MODE, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_fused(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
+            T *__restrict__ accbase, T *__restrict__ outbase, double *__restrict__ red_out,
+            const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, GPW = Gm::GROUPS_PER_WARP;
+    constexpr int NW = NT / 32, NGRP = NT / G;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ridx = work[blockIdx.x];
+    const Replica r = reps[ridx];
+    const int D = r.D, Dpad = r.Dpad, DD = D * D;
+    const long long cs = (long long)D * RS;           // spectrum component stride
+    const long long ms_s = (long long)D * Dpad;       // stage-state component stride
+
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
+    cplx<T> *spec = tw + R1 * G;
+    cplx<T> *scratch = spec + 3 * cs;
+    T *msm = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);
+    double *red = reinterpret_cast<double *>(msm + 3 * ms_s);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    GroupId<P> gid(tid);
+    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
+    const int gw = gid.group % GPW;
+
+    load_twiddles<P>(tw, twP, tid, NT);
+    V3Ptr<T> yn{ybase + r.state_off, ms_s};
+    V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s};
+    V3Ptr<T> out{outbase ? outbase + r.state_off : nullptr, ms_s};
+    V3Ptr<T> ms{msm, ms_s};
+    for (int cell = tid; cell < DD; cell += NT) {
+        const int y = cell / D, x = cell - y * D;
+        const long long si = (long long)y * Dpad + x;
+        vec3<T> v = r.mask[cell] ? yn.ld(si) : vec3<T>{T(0), T(0), T(0)};
+        ms.st(si, v);
+    }
+    __syncthreads();
+
+    const int nrow = row_tasks(D);
+    constexpr int ncol = P / 2;
+    double esum = 0.0;
+    const long long nst = (MODE == M_FIELD || MODE == M_ENERGY) ? 1 : nsteps;
+    for (long long n = 0; n < nst; ++n) {
+        for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
+            for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
+                const int q = qb + gw;
+                row_fwd_task<P, T>(q, q < nrow, D, msm, Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw, gid.gmask);
+            }
+            __syncthreads();
+            for (int qb = warp * GPW; qb < ncol; qb += NW * GPW) {
+                const int q = qb + gw;
+                col_task<P, T>(q, q < ncol, D, spec, cs, reinterpret_cast<const T *>(r.Ghat), gid.t, gid.lane, scr,
+                               tw, gid.gmask);
+            }
+            __syncthreads();
+            for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
+                const int q = qb + gw;
+                row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+            }
+            __syncthreads();
+            const T *hr = reinterpret_cast<const T *>(spec);
+            for (int cell = tid; cell < DD; cell += NT) {
+                if (!r.mask[cell]) continue;
+                const int y = cell / D, x = cell - y * D;
+                const long long si = (long long)y * Dpad + x;
+                const long long hi = (long long)y * (2 * RS) + x;
+                vec3<T> b = {hr[hi] + (T)r.chext[0], hr[2 * cs + hi] + (T)r.chext[1], hr[4 * cs + hi] + (T)r.chext[2]};
+                esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
+            }
+            __syncthreads();
+        }
+    }
+    if (MODE == M_ENERGY) {
+        esum = warp_sum(esum);
+        if ((tid & 31) == 0) red[warp] = esum;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += red[w];
+            red_out[ridx] = s;
+        }
+    }
+}
+
+// ----------------------------------------------------------- global path
+
+template <int P, typename T, int NT>
+__global__ void __launch_bounds__(NT)
+    k_g_rows(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ msbase,
+             cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP, int inverse)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = NT / G;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
+    cplx<T> *scratch = tw + R1 * G;
+    const Replica r = reps[work[blockIdx.y]];
+    const int D = r.D, tid = threadIdx.x;
+    load_twiddles<P>(tw, twP, tid, NT);
+    __syncthreads();
+    GroupId<P> gid(tid);
+    const int q = blockIdx.x * NGRP + gid.group;
+    const int nrow = row_tasks(D);
+    if (blockIdx.x * NGRP >= nrow) return;   // CTA-uniform
+    const long long cs = (long long)D * RS;
+    cplx<T> *spec = specbase + r.spec_off;
+    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
+    if (!inverse) {
+        const long long ms_s = (long long)D * r.Dpad;
+        row_fwd_task<P, T>(q, q < nrow, D, msbase + r.state_off, r.Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw,
+                           gid.gmask);
+    } else {
+        row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+    }
+}
+
+template <int P, typename T, int NT>
+__global__ void __launch_bounds__(NT)
+    k_g_cols(const Replica *__restrict__ reps, const int *__restrict__ work, cplx<T> *__restrict__ specbase,
+             const cplx<T> *__restrict__ twP)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = NT / G;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
+    cplx<T> *scratch = tw + R1 * G;
+    const Replica r = reps[work[blockIdx.y]];
+    const int D = r.D, tid = threadIdx.x;
+    load_twiddles<P>(tw, twP, tid, NT);
+    __syncthreads();
+    GroupId<P> gid(tid);
+    const int q = blockIdx.x * NGRP + gid.group;
+    const long long cs = (long long)D * RS;
+    col_task<P, T>(q, q < P / 2, D, specbase + r.spec_off, cs, reinterpret_cast<const T *>(r.Ghat), gid.t, gid.lane,
+                   scratch + gid.group * Gm::SCRATCH, tw, gid.gmask);
+}
+
+// Elementwise epilogue of the global path.  grid = (cell blocks, replicas).
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256)
+    k_g_epi(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ msbase,
+            T *__restrict__ ybase, T *__restrict__ accbase, T *__restrict__ outbase,
+            const cplx<T> *__restrict__ specbase, double *__restrict__ red_out, int stage,
+            unsigned long long step)
+{
+    constexpr int RS = SpecGeom<P>::RS;
+    const int ridx = work[blockIdx.y];
+    const Replica r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const long long ms_s = (long long)D * r.Dpad, cs = (long long)D * RS;
+    const int cell = blockIdx.x * 256 + threadIdx.x;
+    double e = 0.0;
+    if (cell < DD && r.mask[cell]) {
+        const int y = cell / D, x = cell - y * D;
+        const long long si = (long long)y * r.Dpad + x;
+        const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off);
+        const long long hi = (long long)y * (2 * RS) + x;
+        vec3<T> b = {hr[hi] + (T)r.chext[0], hr[2 * cs + hi] + (T)r.chext[1], hr[4 * cs + hi] + (T)r.chext[2]};
+        V3Ptr<T> ms{msbase + r.state_off, ms_s}, yn{ybase + r.state_off, ms_s};
+        V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s}, out{outbase ? outbase + r.state_off : nullptr, ms_s};
+        e = epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step + r.step0);
+    }
+    if (MODE == M_ENERGY) {
+        __shared__ double red[8];
+        e = warp_sum(e);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < 8; ++w) s += red[w];
+            atomicAdd(red_out + ridx, s);
+        }
+    }
+}
+
+// Copy y_n into the stage buffer (masked), for the global path.
+template <typename T>
+__global__ void k_g_load_stage(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ ybase,
+                               T *__restrict__ msbase)
+{
+    const Replica r = reps[work[blockIdx.y]];
+    const int D = r.D, DD = D * D;
+    const long long ms_s = (long long)D * r.Dpad;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < DD; cell += gridDim.x * blockDim.x) {
+        const int y = cell / D, x = cell - y * D;
+        const long long si = r.state_off + (long long)y * r.Dpad + x;
+        const bool in = r.mask[cell];
+        for (int c = 0; c < 3; ++c) msbase[si + c * ms_s] = in ? ybase[si + c * ms_s] : T(0);
+    }
+}
+
+// --------------------------------------------------------- launch helpers
+
+template <int P> struct FusedNT { static constexpr int v = 512; };
+template <> struct FusedNT<64> { static constexpr int v = 384; };
+template <> struct FusedNT<32> { static constexpr int v = 256; };
+template <> struct FusedNT<16> { static constexpr int v = 128; };
+template <int P> struct GlobNT { static constexpr int v = 256; };
+
+template <int P, typename T, int NT>
+constexpr size_t glob_smem_bytes()
+{
+    return sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G + (size_t)(NT / FFTGeom<P>::G) * FFTGeom<P>::SCRATCH);
+}
+
+template <int P, typename T, int MODE>
+static cudaError_t launch_fused_t(const LaunchArgs &a)
+{
+    constexpr int NT = FusedNT<P>::v;
+    auto kern = k_fused<P, T, MODE, NT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nwork, NT, a.smem, a.stream>>>(a.reps, a.work, (T *)a.y, (T *)a.acc, (T *)a.out, a.red, (const cplx<T> *)a.tw,
+                                            a.nsteps, a.step_base);
+    return cudaGetLastError();
+}
+
+template <int P, typename T>
+static cudaError_t launch_fused_p(const LaunchArgs &a)
+{
+    switch (a.mode) {
+    case M_FIELD: return launch_fused_t<P, T, M_FIELD>(a);
+    case M_ENERGY: return launch_fused_t<P, T, M_ENERGY>(a);
+    case M_RK4: return launch_fused_t<P, T, M_RK4>(a);
+    case M_HEUN: return launch_fused_t<P, T, M_HEUN>(a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, typename T, int MODE>
+static void launch_g_epi(const LaunchArgs &a, dim3 ge, int stage, unsigned long long step)
+{
+    k_g_epi<P, T, MODE><<<ge, 256, 0, a.stream>>>(a.reps, a.work, (T *)a.ms, (T *)a.y, (T *)a.acc, (T *)a.out,
+                                                   (const cplx<T> *)a.spec, a.red, stage, step);
+}
+
+// One field evaluation on the global path: stage buffer -> spectrum -> field.
+template <int P, typename T>
+static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode, unsigned long long step)
+{
+    constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
+    const int nrow = row_tasks(maxD);
+    dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork), gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
+    const size_t sm = glob_smem_bytes<P, T, NT>();
+    k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 0);
+    k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+    k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 1);
+    dim3 ge((maxD * maxD + 255) / 256, a.nwork);
+    switch (mode) {
+    case M_FIELD: launch_g_epi<P, T, M_FIELD>(a, ge, stage, step); break;
+    case M_ENERGY: launch_g_epi<P, T, M_ENERGY>(a, ge, stage, step); break;
+    case M_RK4: launch_g_epi<P, T, M_RK4>(a, ge, stage, step); break;
+    case M_HEUN: launch_g_epi<P, T, M_HEUN>(a, ge, stage, step); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int P, typename T>
+static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
+{
+    constexpr int NT = GlobNT<P>::v;
+    const int sm = (int)glob_smem_bytes<P, T, NT>();
+    cudaError_t e0 = cudaFuncSetAttribute(k_g_rows<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e0 == cudaSuccess) e0 = cudaFuncSetAttribute(k_g_cols<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e0 != cudaSuccess) return e0;
+    dim3 gl((maxD * maxD + 255) / 256, a.nwork);
+    k_g_load_stage<T><<<gl, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.y, (T *)a.ms);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nst = (a.mode == M_RK4) ? 4 : (a.mode == M_HEUN ? 2 : 1);
+    const long long nsteps = (a.mode == M_FIELD || a.mode == M_ENERGY) ? 1 : a.nsteps;
+    for (long long n = 0; n < nsteps; ++n)
+        for (int s = 0; s < nst; ++s) {
+            e = glob_eval<P, T>(a, maxD, s, a.mode, a.step_base + n);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+}  // namespace nd

@@ -1,0 +1,22 @@
+// nd_glob_f32.cu -- instantiations of the global-memory field path in FP32.
+#include "nd_field_impl.cuh"
+
+namespace nd {
+
+ND_DEFINE_TWIDDLE_UPLOAD(upload_tw_glob_f32)
+
+cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD)
+{
+    switch (P) {
+    case 16: return launch_global_p<16, float>(a, maxD);
+    case 32: return launch_global_p<32, float>(a, maxD);
+    case 64: return launch_global_p<64, float>(a, maxD);
+    case 128: return launch_global_p<128, float>(a, maxD);
+    case 256: return launch_global_p<256, float>(a, maxD);
+    case 512: return launch_global_p<512, float>(a, maxD);
+    case 1024: return launch_global_p<1024, float>(a, maxD);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nd

@@ -1,0 +1,59 @@
+// nd_kernels.h -- host-side interface between the C-ABI layer and the CUDA
+// kernels (no CUDA device code here, no torch types).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace nd {
+
+enum { ND_PREC_FP32 = 0, ND_PREC_FP64 = 1 };
+enum { M_FIELD = 0, M_RK4 = 1, M_HEUN = 2, M_ENERGY = 3 };
+
+struct Replica;
+
+struct LaunchArgs {
+    int mode = M_FIELD;
+    const Replica *reps = nullptr;   // device array of all replicas of the handle
+    const int *work = nullptr;       // device array: replica indices handled by this launch
+    int nwork = 0;
+    void *y = nullptr;               // state y_n (user buffer, updated in place by steppers)
+    void *acc = nullptr;             // stage accumulator scratch (same layout as y)
+    void *out = nullptr;             // field output (field mode)
+    void *ms = nullptr;              // global-path stage state (same layout as y)
+    void *spec = nullptr;            // global-path spectrum scratch
+    double *red = nullptr;           // per-replica reduction output (energy), indexed by replica
+    const void *tw = nullptr;        // length-P twiddle table exp(-2 pi i k/P) of the precision
+    long long nsteps = 1;
+    unsigned long long step_base = 0;
+    size_t smem = 0;
+    cudaStream_t stream = 0;
+};
+
+cudaError_t upload_twiddle_constants(const double *re, const double *im);
+size_t fused_smem(int P, int prec, int D, int Dpad);
+cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
+cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD);
+size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] spectrum
+
+// Spectral kernel build (Section II.B tensor, cell self terms, exchange folded in).
+// Gq: optional device table [4][D][D] of a^2 G at displacements (dx, dy) >= 0 (comps xx, yy, xy, zz,
+// self terms at the origin); when null it is computed from the paper's closed forms.
+// Output: Ghat64 [P/2+1][P/2+1][4] doubles and, if Ghat32 != null, a float copy.
+cudaError_t build_ghat(int P, int D, double L_over_a, double Nx, double Nz, double c, const double *Gq_dev,
+                       double *Ghat64, float *Ghat32, double *work, cudaStream_t st);
+size_t build_ghat_work_doubles(int P, int D);
+
+// Auxiliary kernels (nd_aux.cu).
+cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, int nwork, int maxD, void *y,
+                               const double *X0_cells /*[nrep][2], units of a, device*/, const int *pol_chi,
+                               double lambda_over_a, cudaStream_t st);
+cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, const void *y,
+                               double rc2, double *out /*[nrep][4]: xc, yc (units of a), status, pad*/,
+                               cudaStream_t st);
+cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y,
+                          double *out /*[nrep][3]*/, cudaStream_t st);
+cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st);
+cudaError_t launch_check_finite(int prec, const void *y, size_t n, unsigned *flag, cudaStream_t st);
+
+}  // namespace nd

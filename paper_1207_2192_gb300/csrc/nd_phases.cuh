@@ -1,0 +1,295 @@
+// nd_phases.cuh -- the three passes of one demagnetisation + exchange field
+// evaluation (Section II.B convolution done with FFTs), written once and used
+// both by the fused single-CTA kernel (spectrum in shared memory) and by the
+// global-memory path (spectrum in HBM/L2).
+//
+// Spectrum layout: spec[c][y][RS] complex, c = x, y, z; row y = 0..D-1 of the
+// zero-padded P x P grid (rows D..P-1 are zero and never stored); column
+// kx = 0..P/2 of the half spectrum; RS = P/2 + 2 words per row so that the
+// column pass reads conflict-free.  After the inverse row pass the same rows,
+// viewed as real arrays, hold the field b' = exchange + (a^2/lambda^2) h^M.
+//
+// Row pass (forward): the two real rows m_x(y), m_y(y) are transformed as one
+// complex row m_x + i m_y, and the m_z rows are taken in pairs (y, y+1); the
+// two real spectra are separated with the mirror element P-k.
+// Column pass: kx = 1..P/2-1 are complex columns; the two real columns kx = 0
+// and kx = P/2 are packed as one complex column.  Each column is transformed,
+// multiplied by the spectral kernel, and transformed back, keeping rows < D.
+// Row pass (inverse): the Hermitian half rows are completed by conjugation and
+// pairs of real outputs are recovered from one complex inverse transform.
+#pragma once
+#include "nd_fft.cuh"
+
+namespace nd {
+
+template <int P> struct SpecGeom {
+    static constexpr int RS = (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);
+    static constexpr int KH = P / 2 + 1;   // kernel table side
+};
+
+template <typename T> struct GhatVal { T xx, yy, xy, zz; };
+
+template <typename T> __device__ __forceinline__ GhatVal<T> load_ghat(const T *G, int idx);
+template <> __device__ __forceinline__ GhatVal<float> load_ghat<float>(const float *G, int idx)
+{
+    float4 v = __ldg(reinterpret_cast<const float4 *>(G) + idx);
+    return {v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ GhatVal<double> load_ghat<double>(const double *G, int idx)
+{
+    double2 a = __ldg(reinterpret_cast<const double2 *>(G) + 2 * idx);
+    double2 b = __ldg(reinterpret_cast<const double2 *>(G) + 2 * idx + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// Number of row tasks: D complex xy rows plus ceil(D/2) z row pairs.
+__host__ __device__ __forceinline__ int row_tasks(int D) { return D + (D + 1) / 2; }
+
+// ---------------------------------------------------------------- row fwd
+
+// ms: stage magnetisation [3][D][ldm] (zero outside the disk); spec as above
+// with component stride cstride (complex words).
+template <int P, typename T>
+__device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T *ms, int ldm, long long mstride,
+                                             cplx<T> *spec, long long cstride, int t, int lane, cplx<T> *scr,
+                                             const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    const bool isxy = q < D;
+    const int y0 = isxy ? q : 2 * (q - D);
+    const int y1 = y0 + 1;
+    cplx<T> v[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int x = t + G * o;
+        v[o] = {T(0), T(0)};
+        if (active && x < D) {
+            if (isxy) {
+                v[o].x = ms[(long long)y0 * ldm + x];
+                v[o].y = ms[mstride + (long long)y0 * ldm + x];
+            } else {
+                v[o].x = ms[2 * mstride + (long long)y0 * ldm + x];
+                if (y1 < D) v[o].y = ms[2 * mstride + (long long)y1 * ldm + x];
+            }
+        }
+    }
+    fft_group<P, -1>(v, t, scr, tw, gmask);
+    cplx<T> w[R1];
+    mirror_group<P>(v, w, t, lane);
+    if (!active) return;
+    cplx<T> *dA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
+    cplx<T> *dB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
+    const bool hasB = isxy || (y1 < D);
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int k = t + G * o;
+        if (k <= P / 2) {
+            const T h = T(0.5);
+            cplx<T> A = {h * (v[o].x + w[o].x), h * (v[o].y - w[o].y)};
+            cplx<T> B = {h * (v[o].y + w[o].y), -h * (v[o].x - w[o].x)};
+            dA[k] = A;
+            if (hasB) dB[k] = B;
+        }
+    }
+}
+
+// --------------------------------------------------------------- columns
+
+template <int P, typename T>
+__device__ __forceinline__ void col_multiply(cplx<T> *vx, cplx<T> *vy, const T *Ghat, int kx, int t)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH;
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int ky = t + G * o;
+        const bool up = ky <= P / 2;
+        const int kyr = up ? ky : P - ky;
+        GhatVal<T> g = load_ghat<T>(Ghat, kx * KH + kyr);
+        const T gxy = up ? g.xy : -g.xy;     // G_xy is odd in ky
+        cplx<T> a = vx[o], b = vy[o];
+        vx[o] = {g.xx * a.x + gxy * b.x, g.xx * a.y + gxy * b.y};
+        vy[o] = {gxy * a.x + g.yy * b.x, gxy * a.y + g.yy * b.y};
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void col_multiply_z(cplx<T> *vz, const T *Ghat, int kx, int t)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH;
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int ky = t + G * o;
+        const int kyr = ky <= P / 2 ? ky : P - ky;
+        GhatVal<T> g = load_ghat<T>(Ghat, kx * KH + kyr);
+        vz[o] = cscale(vz[o], g.zz);
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void col_load(cplx<T> *v, const cplx<T> *col, int D, int t, bool active)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int y = t + G * o;
+        v[o] = (active && y < D) ? col[(long long)y * RS] : cplx<T>{T(0), T(0)};
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void col_store(const cplx<T> *v, cplx<T> *col, int D, int t, bool active)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    if (!active) return;
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int y = t + G * o;
+        if (y < D) col[(long long)y * RS] = v[o];
+    }
+}
+
+// Column task q = 0..P/2-1: q = 0 is the packed pair of real columns kx = 0
+// and kx = P/2, q >= 1 is column kx = q.
+template <int P, typename T>
+__device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spec, long long cstride,
+                                         const T *Ghat, int t, int lane, cplx<T> *scr, const cplx<T> *tw,
+                                         unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH;
+    if (q > 0) {
+        const int kx = q;
+        cplx<T> vx[R1], vy[R1];
+        col_load<P>(vx, spec + kx, D, t, active);
+        col_load<P>(vy, spec + cstride + kx, D, t, active);
+        fft_group<P, -1>(vx, t, scr, tw, gmask);
+        fft_group<P, -1>(vy, t, scr, tw, gmask);
+        col_multiply<P>(vx, vy, Ghat, kx, t);
+        fft_group<P, +1>(vx, t, scr, tw, gmask);
+        fft_group<P, +1>(vy, t, scr, tw, gmask);
+        col_store<P>(vx, spec + kx, D, t, active);
+        col_store<P>(vy, spec + cstride + kx, D, t, active);
+        cplx<T> vz[R1];
+        col_load<P>(vz, spec + 2 * cstride + kx, D, t, active);
+        fft_group<P, -1>(vz, t, scr, tw, gmask);
+        col_multiply_z<P>(vz, Ghat, kx, t);
+        fft_group<P, +1>(vz, t, scr, tw, gmask);
+        col_store<P>(vz, spec + 2 * cstride + kx, D, t, active);
+        return;
+    }
+    // packed real columns: z = c0 + i c_{P/2}; G_xy vanishes on both columns
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        cplx<T> *col = spec + c * cstride;
+        cplx<T> v[R1];
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int y = t + G * o;
+            v[o] = {T(0), T(0)};
+            if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
+        }
+        fft_group<P, -1>(v, t, scr, tw, gmask);
+        cplx<T> w[R1];
+        mirror_group<P>(v, w, t, lane);
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int ky = t + G * o;
+            const int kyr = ky <= P / 2 ? ky : P - ky;
+            GhatVal<T> g0 = load_ghat<T>(Ghat, kyr);
+            GhatVal<T> g1 = load_ghat<T>(Ghat, (P / 2) * KH + kyr);
+            const T s0 = c == 0 ? g0.xx : (c == 1 ? g0.yy : g0.zz);
+            const T s1 = c == 0 ? g1.xx : (c == 1 ? g1.yy : g1.zz);
+            const T h = T(0.5);
+            cplx<T> F0 = {h * (v[o].x + w[o].x), h * (v[o].y - w[o].y)};
+            cplx<T> F1 = {h * (v[o].y + w[o].y), -h * (v[o].x - w[o].x)};
+            F0 = cscale(F0, s0);
+            F1 = cscale(F1, s1);
+            v[o] = {F0.x - F1.y, F0.y + F1.x};
+        }
+        fft_group<P, +1>(v, t, scr, tw, gmask);
+        if (active) {
+#pragma unroll
+            for (int o = 0; o < R1; ++o) {
+                const int y = t + G * o;
+                if (y < D) {
+                    col[(long long)y * RS] = {v[o].x, T(0)};
+                    col[(long long)y * RS + P / 2] = {v[o].y, T(0)};
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- row inv
+
+template <int P, typename T>
+__device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> *spec, long long cstride, int t,
+                                             cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    const bool isxy = q < D;
+    const int y0 = isxy ? q : 2 * (q - D);
+    const int y1 = y0 + 1;
+    const bool hasB = isxy || (y1 < D);
+    cplx<T> *rA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
+    cplx<T> *rB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
+    cplx<T> v[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int k = t + G * o;
+        const bool up = k <= P / 2;
+        const int kk = up ? k : P - k;
+        cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
+        if (active) {
+            a = rA[kk];
+            if (hasB) b = rB[kk];
+        }
+        if (!up) { a.y = -a.y; b.y = -b.y; }
+        v[o] = {a.x - b.y, a.y + b.x};
+    }
+    fft_group<P, +1>(v, t, scr, tw, gmask);
+    if (!active) return;
+    T *oA = reinterpret_cast<T *>(rA), *oB = reinterpret_cast<T *>(rB);
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int x = t + G * o;
+        if (x < D) {
+            oA[x] = v[o].x;
+            if (hasB) oB[x] = v[o].y;
+        }
+    }
+}
+
+// --------------------------------------------------------- group plumbing
+
+template <int P> struct GroupId {
+    int group, t, lane;
+    unsigned gmask;
+    __device__ __forceinline__ GroupId(int tid)
+    {
+        constexpr int G = FFTGeom<P>::G;
+        lane = tid & 31;
+        group = tid / G;
+        t = tid & (G - 1);
+        gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    }
+};
+
+// Fill the [R1][G] twiddle table exp(-2 pi i t k1 / P) from the length-P table.
+template <int P, typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T> *tw, const cplx<T> *twP, int tid, int nthreads)
+{
+    constexpr int G = FFTGeom<P>::G, R1 = FFTGeom<P>::R1;
+    for (int i = tid; i < R1 * G; i += nthreads) {
+        const int k1 = i / G, t = i % G;
+        tw[i] = twP[(k1 * t) % P];
+    }
+}
+
+}  // namespace nd
