@@ -76,7 +76,7 @@ __device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T 
     }
     fft_group<P, -1>(v, t, scr, tw, gmask);
     cplx<T> w[R1];
-    mirror_group<P>(v, w, t, lane);
+    mirror_group<P>(v, w, t, lane, gmask);
     if (!active) return;
     cplx<T> *dA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
     cplx<T> *dB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
@@ -163,7 +163,7 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH;
     if (q > 0) {
-        const int kx = q;
+        const int kx = active ? q : 1;   // idle groups still run the transforms; keep their table reads in range
         cplx<T> vx[R1], vy[R1];
         col_load<P>(vx, spec + kx, D, t, active);
         col_load<P>(vy, spec + cstride + kx, D, t, active);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
         }
         fft_group<P, -1>(v, t, scr, tw, gmask);
         cplx<T> w[R1];
-        mirror_group<P>(v, w, t, lane);
+        mirror_group<P>(v, w, t, lane, gmask);
 #pragma unroll
         for (int o = 0; o < R1; ++o) {
             const int ky = t + G * o;
