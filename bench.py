@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: LLG cell-updates per second on one or more GB300s.
+
+Workload (default "batched_heun"): 256 replicas of a Permalloy disk R = 50 nm,
+L = 10 nm, a = 2 nm (50 x 50 cells, 1976 in the disk, FFT grid 128 x 128),
+T = 300 K, alpha = 0.01, dt = 10 fs, Philox seeds 0..255, FP32 fields -- the
+batched Langevin-Heun configuration.  One bench step is CHUNK = 50 stochastic
+Heun time steps of every replica (two full field evaluations each) followed
+by the per-replica observables the statistics need (vortex core position and
+<m>).  A cell-update is one time step of one disk cell of one replica.
+
+Other workloads: "large_disk" (8 replicas of R = 500 nm, L = 20 nm, FFT grid
+1024 x 1024, Heun at 300 K) and "plain" (the batched workload's disk as a
+single replica).
+
+The JSON line also carries: the plain single-replica number (batched vs
+plain), the roofline of the dominant kernel, the end-to-end number through the
+C ABI with host buffers, SM clocks sampled during the timed region, and the
+FP64 CPU oracle timed on the host cores.  With --impl reference the oracle
+alone is timed as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHUNK = 50          # Heun steps per bench step
+DT = 1e-14          # 10 fs
+T_K = 300.0
+ALPHA = 0.01
+
+WORKLOADS = {
+    "batched_heun": dict(R=50e-9, L=10e-9, B=256),
+    "plain": dict(R=50e-9, L=10e-9, B=1),
+    "large_disk": dict(R=500e-9, L=20e-9, B=8),
+}
+
+
+def fft_flops_per_eval(P, C):
+    """Algorithmic flops of one field evaluation: 2.5 P^2 log2(P^2) per real 2D
+    transform (three forward, three inverse), 14 per spectral point of the
+    tensor multiply, 60 per cell for the epilogue."""
+    import math
+    return 6 * 2.5 * P * P * math.log2(P * P) + 14 * P * (P // 2 + 1) + 60 * C
+
+
+def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152, lanes=128):
+    """FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock."""
+    return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/nd_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]) if parts[3] not in ("[N/A]", "") else None,
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("swp", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------- GPU workload
+
+class Workload:
+    def __init__(self, name, device):
+        import torch
+        import paper_1207_2192_gb300 as nd
+        self.nd, self.torch = nd, torch
+        w = WORKLOADS[name]
+        self.name = name
+        self.disk = nd.Disk(w["R"], w["L"], alpha=ALPHA)
+        self.B = w["B"]
+        self.h = nd.Nanodisk([self.disk], [self.B], nd.ND_FP32)
+        L0 = self.h.layout[0]
+        self.D, self.P, self.C = L0["D"], L0["P"], L0["cells"]
+        self.m = self.h.empty_device()
+        self.h.init_vortex(self.m, np.zeros((self.B, 2)))
+        self.T = np.full(self.B, T_K)
+        self.seeds = np.arange(self.B, dtype=np.uint64)
+        self.step = 0
+        self.stream = torch.cuda.current_stream()
+
+    def cell_updates_per_step(self):
+        return self.B * self.C * CHUNK
+
+    def run_step(self, m=None):
+        """One bench step: CHUNK Heun steps + observables.  Returns launches."""
+        target = self.m if m is None else m
+        self.h.heun(target, CHUNK, DT, self.T, self.seeds, step0=self.step, stream=self.stream)
+        self.step += CHUNK
+        self.h.vortex_core(target, stream=self.stream)
+        self.h.mean_m(target, stream=self.stream)
+        return 3
+
+
+def l2_flush(torch, buf):
+    buf.add_(1.0)   # writes 256 MB > 129 MB L2
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = Workload(args.workload, local_rank)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        wl.run_step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            l2_flush(torch, flush)
+            ev[i][0].record()
+            kev[i][0].record()
+            wl.h.heun(wl.m, CHUNK, DT, wl.T, wl.seeds, step0=wl.step, stream=wl.stream)
+            kev[i][1].record()
+            wl.step += CHUNK
+            wl.h.vortex_core(wl.m, stream=wl.stream)
+            wl.h.mean_m(wl.m, stream=wl.stream)
+            ev[i][1].record()
+            launches += 3
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cu = wl.cell_updates_per_step() * args.steps * world
+    value = cu / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    host = torch.empty(wl.h.state_elems, dtype=torch.float32, pin_memory=True)
+    host.copy_(wl.m.cpu())
+    nbytes = host.numel() * host.element_size()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        wl.nd.nd_step_heun(wl.h.h, host.data_ptr(), CHUNK, DT, wl.T, wl.seeds, wl.step, None)
+        wl.step += CHUNK
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = cu / e2e_s
+
+    result = None
+    if rank == 0:
+        peaks = measured_peaks()
+        clocks = clk.summary()
+        flop_cu = 2 * fft_flops_per_eval(wl.P, wl.C) / wl.C          # per cell-update (Heun = 2 evaluations)
+        kern_avg_s = statistics.mean(kern_ms) / 1e3
+        achieved = flop_cu * wl.cell_updates_per_step() / kern_avg_s / 1e12
+        peak = fp32_alu_peak_tflops()
+        result = {
+            "metric": "LLG cell-updates/sec", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (analytic centred vortex, Philox thermal noise)",
+            "config": {"workload": args.workload, "replicas_per_gpu": wl.B, "R_nm": wl.disk.R * 1e9,
+                       "L_nm": wl.disk.L * 1e9, "a_nm": wl.disk.a * 1e9, "D": wl.D, "cells": wl.C, "P": wl.P,
+                       "T_K": T_K, "alpha": ALPHA, "dt_fs": DT * 1e15, "heun_steps_per_bench_step": CHUNK,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_fused<P,float,HEUN>", "flops_per_cell_update": flop_cu,
+                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (no FP32 entry in MEASURED_PEAKS.json)"},
+            "kernel_ms_per_step": statistics.mean(kern_ms),
+            "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if "hbm_gbs" in peaks:
+            result["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    if dist:
+        dist.destroy_process_group()
+    return result, wl
+
+
+def plain_number(args):
+    """Batched-vs-plain: the same disk as one replica, same kernels and accuracy."""
+    import torch
+    wl = Workload("plain", 0)
+    for _ in range(3):
+        wl.run_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, args.steps)
+    a.record()
+    for _ in range(n):
+        wl.run_step()
+    b.record()
+    torch.cuda.synchronize()
+    return wl.cell_updates_per_step() * n / (a.elapsed_time(b) / 1e3)
+
+
+# ---------------------------------------------------------------- oracle
+
+def oracle_rate(workload, budget_s=12.0):
+    """FP64 direct-sum oracle, as it stands, on the host cores: Heun steps of
+    one replica of the workload's disk.  Returns (cell-updates/s, sample)."""
+    import oracle
+    w = WORKLOADS[workload]
+    model = oracle.Model(w["R"], w["L"], alpha=ALPHA)
+    m = model.init_vortex(0.0, 0.0)
+    if model.C > 20000:
+        # a full step is out of reach (C^2 pair terms per evaluation): time the
+        # direct-sum field at k sampled cells and extrapolate (2 evaluations per step)
+        cells = np.flatnonzero(model.mask.ravel())[:: max(1, model.C // 64)][:64]
+        t0 = time.perf_counter()
+        model.field_at(m, cells)
+        el = time.perf_counter() - t0
+        rate = len(cells) / (2.0 * el)
+        return rate, (f"extrapolated: direct-sum field at {len(cells)} of {model.C} cells of one "
+                      f"R={w['R']*1e9:.0f} nm replica in {el:.1f} s, 2 evaluations per Heun step"), oracle.num_threads()
+    Ts = oracle.scaled_temperature(T_K, model.A, model.L)
+    dtau = model.dtau(DT)
+    t0 = time.perf_counter()
+    model.heun(m, 1, dtau, Ts, 0, 0)
+    one = time.perf_counter() - t0
+    n = max(1, min(2000, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    model.heun(m, n, dtau, Ts, 0, 1)
+    el = time.perf_counter() - t0
+    rate = model.C * n / el
+    return rate, f"{n} Heun steps of one R={w['R']*1e9:.0f} nm replica ({model.C} cells), {el:.1f} s", oracle.num_threads()
+
+
+def run_reference(args):
+    rates = []
+    sample = ""
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        r, sample, cores = oracle_rate(args.workload, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    return {
+        "impl": "reference", "metric": "LLG cell-updates/sec", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_heun", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    result, wl = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_plain and args.workload == "batched_heun":
+            plain = plain_number(args)
+            result["plain"] = {"value": plain, "unit": "cell-updates/s", "replicas": 1,
+                               "batched_over_plain": result["value"] / world / plain}
+        if not args.no_cpu_baseline:
+            rate, sample, cores = oracle_rate(args.workload)
+            result["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                                      "sample": sample}
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,10 @@ static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const d
         R.flags = (R.sigma > 0.0) ? 1 : 0;
         R.seed = seed ? seed[r] : 0ull;
         R.step0 = step0;
+        for (int k = 0; k < 3; ++k) R.fchext[k] = (float)R.chext[k];
+        R.falpha = (float)R.alpha;
+        R.fdtau = (float)R.dtau;
+        R.fsigma = (float)R.sigma;
     }
 }
 

@@ -58,12 +58,12 @@ template <> __device__ __forceinline__ vec3<float> thermal_normals<float>(uint64
     uint4 r = philox4x32_10(make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u), (uint32_t)seed,
                             (uint32_t)(seed >> 32));
     const float s32 = 2.3283064365386963e-10f;
-    // (r + 1) 2^-32 formed in double then rounded once, so u > 0 for every r
-    float u0 = (float)(((double)r.x + 1.0) * 2.3283064365386963e-10), u2 = (float)(((double)r.z + 1.0) * 2.3283064365386963e-10);
+    // u = (r + 1) 2^-32 in (0, 1]: the word rounded to float, scaled exactly, then offset
+    float u0 = __fmaf_rn(__uint2float_rn(r.x), s32, s32), u2 = __fmaf_rn(__uint2float_rn(r.z), s32, s32);
     float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
     float s1, c1, s3, c3;
-    sincospif(2.0f * (float)r.y * s32, &s1, &c1);
-    sincospif(2.0f * (float)r.w * s32, &s3, &c3);
+    sincospif(2.0f * __uint2float_rn(r.y) * s32, &s1, &c1);
+    sincospif(2.0f * __uint2float_rn(r.w) * s32, &s3, &c3);
     return {ra * c1, ra * s1, rb * c3};
 }
 
@@ -94,7 +94,22 @@ struct Replica {
     double chext[3];             // (a^2/lambda^2) h_ext
     double alpha, dtau, sigma;   // damping, dimensionless step, noise amplitude
     unsigned long long seed, step0;
+    float fchext[3];             // single-precision copies for the FP32 kernels
+    float falpha, fdtau, fsigma;
 };
+
+// Stepping parameters in the kernel's precision (no double arithmetic in the
+// FP32 kernels: GB300's FP64 rate is a small fraction of its FP32 rate).
+template <typename T> struct StepParams { T chext[3], alpha, dtau, sigma; };
+template <typename T> __device__ __forceinline__ StepParams<T> step_params(const Replica &r);
+template <> __device__ __forceinline__ StepParams<float> step_params<float>(const Replica &r)
+{
+    return {{r.fchext[0], r.fchext[1], r.fchext[2]}, r.falpha, r.fdtau, r.fsigma};
+}
+template <> __device__ __forceinline__ StepParams<double> step_params<double>(const Replica &r)
+{
+    return {{r.chext[0], r.chext[1], r.chext[2]}, r.alpha, r.dtau, r.sigma};
+}
 
 // Status word written by kernels (bit flags), read by the host after a sync.
 enum : unsigned { ND_DEV_NAN = 1u, ND_DEV_TIMEOUT = 2u };

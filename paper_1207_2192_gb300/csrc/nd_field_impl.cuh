@@ -65,7 +65,8 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
                                                 V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
                                                 unsigned long long step)
 {
-    const T alpha = (T)r.alpha, dt = (T)r.dtau;
+    const StepParams<T> sp = step_params<T>(r);
+    const T alpha = sp.alpha, dt = sp.dtau;
     vec3<T> m = ms.ld(mi);
     if (MODE == M_FIELD) {
         out.st(si, b);
@@ -93,7 +94,7 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
         }
         return 0.0;
     } else if (MODE == M_HEUN) {
-        const T sig = (T)r.sigma;
+        const T sig = sp.sigma;
         vec3<T> g = {b.x * dt, b.y * dt, b.z * dt};
         if (r.flags & 1) {
             vec3<T> w = thermal_normals<T>(r.seed, (uint32_t)cell, step);
@@ -203,13 +204,17 @@ __global__ void __launch_bounds__(NT, 1)
             }
             __syncthreads();
             const T *hr = reinterpret_cast<const T *>(spec);
+            const StepParams<T> sp = step_params<T>(r);
             for (int cell = tid; cell < DD; cell += NT) {
                 if (!r.mask[cell]) continue;
                 const int y = cell / D, x = cell - y * D;
                 const long long si = (long long)y * Dpad + x;
                 const long long hi = (long long)y * (2 * RS) + x;
-                vec3<T> b = {hr[hi] + (T)r.chext[0], hr[2 * cs + hi] + (T)r.chext[1], hr[4 * cs + hi] + (T)r.chext[2]};
-                esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
+                vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                if (MODE == M_ENERGY)
+                    esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
+                else
+                    epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
             }
             __syncthreads();
         }
@@ -299,7 +304,8 @@ __global__ void __launch_bounds__(256)
         const long long si = (long long)y * r.Dpad + x;
         const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off);
         const long long hi = (long long)y * (2 * RS) + x;
-        vec3<T> b = {hr[hi] + (T)r.chext[0], hr[2 * cs + hi] + (T)r.chext[1], hr[4 * cs + hi] + (T)r.chext[2]};
+        const StepParams<T> sp = step_params<T>(r);
+        vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
         V3Ptr<T> ms{msbase + r.state_off, ms_s}, yn{ybase + r.state_off, ms_s};
         V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s}, out{outbase ? outbase + r.state_off : nullptr, ms_s};
         e = epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step + r.step0);
