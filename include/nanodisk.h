@@ -173,6 +173,38 @@ int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, voi
  * out is a host array [B][3].  Synchronises `stream`. */
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free Heun stepping.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * inside a framework that owns every device allocation through its own pool,
+ * real-time loops that cannot afford an allocation's implicit synchronisation,
+ * or plugins that may only touch the buffers their host gives them.  Such a
+ * caller cannot create a handle, so the disk is described directly.
+ *
+ * The call performs the same n_steps stochastic Heun steps as nd_step_heun on
+ * a handle holding n_replicas replicas of *disk in ND_FP32 (same state layout:
+ * replica r at element offset r * 3 * D * Dpad), with the same noise stream.
+ * Its working memory -- the stage accumulator, the spectral kernel, the mask,
+ * the twiddles and the parameter blocks -- lives in one file-scope device
+ * array of fixed size that every GPU loading the library holds until exit
+ * (about 9 MiB); nothing is allocated.  Limits, rejected with ND_ERR_ARG and
+ * a message: padded grid P <= 128 (disk diameter up to 64 cells, and the
+ * on-chip kernel must fit, about 60 cells), n_replicas <= ND_NOALLOC_MAX_REPLICAS,
+ * n_replicas * 3 * D * Dpad <= ND_NOALLOC_MAX_STATE_FLOATS, and m must be a
+ * device pointer.
+ *
+ * The first call on a device resolves the array's address on that device and
+ * loads the FFT constants; make that first call before any stream capture.
+ * A call with a new geometry rebuilds the spectral kernel and synchronises
+ * `stream`.  Every call shares the array and leaves its contents behind, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race.
+ */
+#define ND_NOALLOC_MAX_STATE_FLOATS (1 << 21)
+#define ND_NOALLOC_MAX_REPLICAS 4096
+int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, float *m, long long n_steps, double dt_seconds,
+                         const double *T_kelvin, const unsigned long long *seed, unsigned long long step0,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

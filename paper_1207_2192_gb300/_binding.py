@@ -58,6 +58,7 @@ SIGNATURES = {
     "nd_init_vortex": (_I, [_P, _P, _P, _P]),
     "nd_vortex_core": (_I, [_P, _P, _P, _P, _P]),
     "nd_mean_m": (_I, [_P, _P, _P, _P]),
+    "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
 }
 
 
@@ -202,3 +203,16 @@ def nd_mean_m(h, m, nrep, stream=None):
     out = np.zeros((nrep, 3))
     _check(lib().nd_mean_m(h, _ptr(m), _ptr(out), _stream(stream)))
     return out
+
+
+def nd_step_heun_noalloc(disk, n_replicas, m, n_steps, dt_seconds, T_kelvin, seed, step0=0, stream=None,
+                         check=True):
+    """Allocation-free Heun steps (no handle); returns the status code."""
+    d = disk if isinstance(disk, nd_disk_desc) else disk.desc()
+    T = np.ascontiguousarray(T_kelvin, dtype=np.float64)
+    s = np.ascontiguousarray(seed, dtype=np.uint64)
+    rc = lib().nd_step_heun_noalloc(ctypes.byref(d), n_replicas, _ptr(m), n_steps, dt_seconds, _ptr(T), _ptr(s),
+                                    step0, _stream(stream))
+    if check:
+        _check(rc)
+    return rc

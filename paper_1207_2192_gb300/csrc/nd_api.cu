@@ -74,6 +74,10 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
+namespace nd {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}
+
 struct nd_handle {
     int prec = ND_FP32;
     int device = 0;
