@@ -156,6 +156,24 @@ int nd_step_rk4(nd_handle *h, void *m, long long n_steps, double dt_seconds, voi
 int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, const double *T_kelvin,
                  const unsigned long long *seed, unsigned long long step0, void *stream);
 
+/* Lagrange-constrained relaxation pinning each replica's vortex core at
+ * X[r] (host array [B][2], metres) (Sec. IV local spin alignment with the
+ * fictitious constraint fields of a Lagrange multiplier; the constraint form
+ * is a reading, the paper defers its details to a cited reference):
+ *   C_k(m) = sum_{i in W} (m_i^z)^2 (r_ik - X_k)/a = 0, k = x, y, with the
+ *   window W = disk cells with |r_i - X| < 4 lambda_ex.
+ * Each sweep evaluates b (Eq. Bi), adds 2 lambda_k m_i^z (r_ik - X_k)/a zhat in
+ * W, stops if max_i |m_i x e_i|/|e_i| < tol, otherwise takes one Newton step
+ * on the two multipliers for C(m') = 0 with the exact 2x2 Jacobian and sets
+ * m_i <- normalise(m_i/2 + e_i/(2|e_i|)).  Multipliers start at zero.  m is
+ * updated in place.  Outputs (host arrays, any may be NULL): U_out[B] the
+ * double-precision energy of the relaxed state (units of J), lambda_out[B][2],
+ * iters_out[B] sweeps applied.  Runs on the on-chip kernel only (P <= 128 in
+ * ND_FP32, P <= 64 in ND_FP64), otherwise ND_ERR_ARG.  Returns
+ * ND_ERR_NOT_CONVERGED if a replica reached max_iter.  Synchronises `stream`. */
+int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int max_iter, double *U_out,
+                         double *lambda_out, int *iters_out, void *stream);
+
 /* Analytic q = +1 vortex centred at X0[r] = (x0, y0) metres (host array
  * [B][2]) for every replica (Sec. IV profile): in-plane angle atan2(y - y0,
  * x - x0) + chirality pi/2, m_z = polarity exp(-rho^2/lambda_ex^2), |m| = 1. */

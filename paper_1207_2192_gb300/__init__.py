@@ -15,13 +15,13 @@ from . import _binding as _b
 from ._binding import (ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NAN, ND_ERR_NO_VORTEX, ND_ERR_NOT_CONVERGED, ND_ERR_TIMEOUT,
                        ND_FP32, ND_FP64, ND_OK, NDError, nd_create_disk, nd_destroy, nd_disk_desc, nd_disk_mask,
                        nd_effective_field, nd_energy, nd_get_info, nd_init_vortex, nd_last_error, nd_mean_m,
-                       nd_replica_layout, nd_set_damping, nd_set_green_tensor, nd_step_heun, nd_step_rk4, nd_units,
-                       nd_vortex_core)
+                       nd_relax_constrained, nd_replica_layout, nd_set_damping, nd_set_green_tensor, nd_step_heun,
+                       nd_step_rk4, nd_units, nd_vortex_core)
 
 __all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "nd_create_disk", "nd_destroy", "nd_effective_field",
            "nd_energy", "nd_step_rk4", "nd_step_heun", "nd_init_vortex", "nd_vortex_core", "nd_mean_m",
            "nd_set_green_tensor", "nd_set_damping", "nd_units", "nd_replica_layout", "nd_get_info",
-           "nd_disk_mask", "nd_last_error"]
+           "nd_disk_mask", "nd_last_error", "nd_relax_constrained"]
 
 
 @dataclass
@@ -135,6 +135,11 @@ class Nanodisk:
 
     def vortex_core(self, m, stream=None):
         return nd_vortex_core(self.h, m, self.B, stream)
+
+    def relax(self, m, X, tol=1e-6, max_iter=20000, stream=None):
+        """Constrained relaxation in place; returns (status, U, lambda, iters)."""
+        return nd_relax_constrained(self.h, m, np.asarray(X, dtype=np.float64).reshape(self.B, 2), self.B, tol,
+                                    max_iter, stream)
 
     def mean_m(self, m, stream=None):
         return nd_mean_m(self.h, m, self.B, stream)

@@ -58,6 +58,7 @@ SIGNATURES = {
     "nd_init_vortex": (_I, [_P, _P, _P, _P]),
     "nd_vortex_core": (_I, [_P, _P, _P, _P, _P]),
     "nd_mean_m": (_I, [_P, _P, _P, _P]),
+    "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
 }
 
@@ -183,6 +184,19 @@ def nd_step_heun(h, m, n_steps, dt_seconds, T_kelvin, seed, step0=0, stream=None
     T = np.ascontiguousarray(T_kelvin, dtype=np.float64)
     s = np.ascontiguousarray(seed, dtype=np.uint64)
     _check(lib().nd_step_heun(h, _ptr(m), n_steps, dt_seconds, _ptr(T), _ptr(s), step0, _stream(stream)))
+
+
+def nd_relax_constrained(h, m, X, nrep, tol=1e-6, max_iter=20000, stream=None, check=True):
+    """Constrained relaxation; returns (status, U[B], lambda[B,2], iters[B])."""
+    Xa = np.ascontiguousarray(X, dtype=np.float64).reshape(nrep, 2)
+    U = np.zeros(nrep)
+    lam = np.zeros((nrep, 2))
+    it = np.zeros(nrep, dtype=np.int32)
+    rc = lib().nd_relax_constrained(h, _ptr(m), _ptr(Xa), tol, max_iter, _ptr(U), _ptr(lam), _ptr(it),
+                                    _stream(stream))
+    if check and rc not in (ND_OK, ND_ERR_NOT_CONVERGED):
+        _check(rc)
+    return rc, U, lam, it
 
 
 def nd_init_vortex(h, m, X0, stream=None):

@@ -106,16 +106,19 @@ struct nd_handle {
     double *red_h = nullptr;              // pinned [B * 4]
     double *aux_d = nullptr;              // [B * 4] small per-replica inputs/outputs
     int *aux_i = nullptr;                 // [B * 2]
+    RelaxIO *rio_d = nullptr;             // [B] relaxation inputs/outputs
+    RelaxIO *rio_h = nullptr;             // pinned [B]
     size_t max_smem = 0;
 };
 
 static int setup_class_paths(nd_handle *h)
 {
     for (auto &c : h->classes) {
+        // 1 KiB of the per-block limit is left for the kernels' static shared variables
         c.smem_main = fused_smem(c.P, h->prec, c.maxD, c.maxDpad);
-        c.fused_main = c.smem_main != (size_t)-1 && c.smem_main <= h->max_smem;
+        c.fused_main = c.smem_main != (size_t)-1 && c.smem_main + 1024 <= h->max_smem;
         c.smem_fp64 = fused_smem(c.P, ND_PREC_FP64, c.maxD, c.maxDpad);
-        c.fused_fp64 = c.smem_fp64 != (size_t)-1 && c.smem_fp64 <= h->max_smem;
+        c.fused_fp64 = c.smem_fp64 != (size_t)-1 && c.smem_fp64 + 1024 <= h->max_smem;
     }
     return ND_OK;
 }
@@ -366,6 +369,8 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     if ((e = cudaMalloc(&h->aux_d, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->aux_i, sizeof(int) * 2 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->acc, h->elt * h->state_elems)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->rio_d, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&h->rio_h, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
     bool any_global = false, any_global64 = false;
     for (auto &c : h->classes) { any_global |= !c.fused_main; any_global64 |= !c.fused_fp64; }
     if (any_global || any_global64) {
@@ -408,6 +413,8 @@ void nd_destroy(nd_handle *h)
     cudaFreeHost(h->red_h);
     cudaFree(h->aux_d);
     cudaFree(h->aux_i);
+    cudaFree(h->rio_d);
+    cudaFreeHost(h->rio_h);
     cudaFree(h->acc);
     cudaFree(h->ms);
     cudaFree(h->spec);
@@ -560,6 +567,71 @@ int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, co
         if (int rc = run_mode(h, M_HEUN, false, md, nullptr, n_steps, st)) return rc;
     }
     return stage_out(h, m, md, st);
+}
+
+int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int max_iter, double *U_out,
+                         double *lambda_out, int *iters_out, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!X) return fail(ND_ERR_ARG, "null X");
+    if (max_iter < 0 || !(tol > 0)) return fail(ND_ERR_ARG, "max_iter must be >= 0 and tol > 0");
+    for (auto &c : h->classes)
+        if (!c.fused_main)
+            return fail(ND_ERR_ARG, "relaxation runs on the on-chip kernel only (P <= 128 in FP32, P <= 64 in FP64)");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    const int B = (int)h->rep_disk.size();
+    ND_CUDA(cudaStreamSynchronize(st));   // the pinned relaxation block is rewritten below
+    for (int r = 0; r < B; ++r) {
+        const DiskInfo &d = h->disks[h->rep_disk[r]];
+        RelaxIO &R = h->rio_h[r];
+        R.X[0] = X[2 * r] / d.desc.a;
+        R.X[1] = X[2 * r + 1] / d.desc.a;
+        R.lam[0] = R.lam[1] = 0.0;
+        R.resid = 0.0;
+        R.iters = 0;
+        R.status = 1;
+    }
+    ND_CUDA(cudaMemcpyAsync(h->rio_d, h->rio_h, sizeof(RelaxIO) * B, cudaMemcpyHostToDevice, st));
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        const double rcut = 4.0 * d.lambda / d.desc.a;
+        LaunchArgs a;
+        a.mode = M_RELAX;
+        a.reps = h->reps_d;
+        a.work = c.work_d;
+        a.nwork = (int)c.reps.size();
+        a.y = md;
+        a.red = h->red_d;
+        a.tw = (prec == ND_PREC_FP64) ? h->tw64[c.P] : h->tw32[c.P];
+        a.smem = c.smem_main;
+        a.stream = st;
+        a.rio = h->rio_d;
+        a.eta = 0.5;
+        a.tol = tol;
+        a.rc2 = rcut * rcut;
+        a.max_iter = max_iter;
+        ND_CUDA(launch_fused(c.P, prec, a));
+    }
+    ND_CUDA(cudaMemcpyAsync(h->rio_h, h->rio_d, sizeof(RelaxIO) * B, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    int rc = ND_OK;
+    for (int r = 0; r < B; ++r) {
+        if (lambda_out) { lambda_out[2 * r] = h->rio_h[r].lam[0]; lambda_out[2 * r + 1] = h->rio_h[r].lam[1]; }
+        if (iters_out) iters_out[r] = h->rio_h[r].iters;
+        if (h->rio_h[r].status != 0) rc = ND_ERR_NOT_CONVERGED;
+    }
+    if (U_out) {
+        int e = nd_energy(h, md, U_out, nullptr, stream);
+        if (e) return e;
+    }
+    if (int e = stage_out(h, m, md, st)) return e;
+    if (rc) g_err = "relaxation did not converge within max_iter in at least one replica";
+    return rc;
 }
 
 int nd_init_vortex(nd_handle *h, void *m, const double *X0, void *stream)

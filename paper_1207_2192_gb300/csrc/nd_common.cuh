@@ -111,6 +111,15 @@ template <> __device__ __forceinline__ StepParams<double> step_params<double>(co
     return {{r.chext[0], r.chext[1], r.chext[2]}, r.alpha, r.dtau, r.sigma};
 }
 
+// Per-replica inputs and outputs of the constrained relaxation.
+struct RelaxIO {
+    double X[2];      // constraint centre in cell units relative to the grid centre
+    double lam[2];    // Lagrange multipliers (start values in, final values out)
+    double resid;     // residual max |m x e|/|e| of the last sweep
+    int iters;        // sweeps applied
+    int status;       // 0 converged, 1 max_iter reached
+};
+
 // Status word written by kernels (bit flags), read by the host after a sync.
 enum : unsigned { ND_DEV_NAN = 1u, ND_DEV_TIMEOUT = 2u };
 

@@ -111,6 +111,45 @@ __device__ __forceinline__ void dft_reg(cplx<T> *v)
     for (int i = 0; i < N; ++i) v[i] = u[i];
 }
 
+// N-point DFT of an input whose upper half is zero (v[j] = 0 for j >= N/2):
+// even outputs are the N/2-point DFT of v, odd outputs that of v[j] w^j.
+template <int N, int DIR, typename T>
+__device__ __forceinline__ void dft_reg_halfin(cplx<T> *v)
+{
+    cplx<T> a[N / 2], b[N / 2];
+#pragma unroll
+    for (int j = 0; j < N / 2; ++j) {
+        a[j] = v[j];
+        b[j] = twid<DIR>(v[j], j, N);
+    }
+    dft_reg<N / 2, DIR>(a);
+    dft_reg<N / 2, DIR>(b);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+    }
+}
+
+// N-point DFT of which only the outputs k < N/2 are needed (the others are
+// left undefined): X[k] = A[k] + w^k B[k] over the even/odd halves.
+template <int N, int DIR, typename T>
+__device__ __forceinline__ void dft_reg_halfout(cplx<T> *v)
+{
+    cplx<T> a[N / 2], b[N / 2];
+#pragma unroll
+    for (int j = 0; j < N / 2; ++j) {
+        a[j] = v[2 * j];
+        b[j] = v[2 * j + 1];
+    }
+    dft_reg<N / 2, DIR>(a);
+    dft_reg<N / 2, DIR>(b);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) v[k] = cadd(a[k], twid<DIR>(b[k], k, N));
+}
+
+enum : int { FFT_FULL = 0, FFT_HALF_IN = 1, FFT_HALF_OUT = 2 };
+
 // Full P-point transform on a group of G threads.
 //   v      : the thread's R1 points, element t + G*o in v[o]; replaced by the
 //            transform in the same layout
@@ -118,12 +157,16 @@ __device__ __forceinline__ void dft_reg(cplx<T> *v)
 //   scr    : this group's private shared scratch, FFTGeom<P>::SCRATCH words
 //   tw     : shared twiddle table [R1][G], tw[k1*G + t] = exp(-2 pi i t k1 / P)
 //   gmask  : lane mask of the group (for __syncwarp)
-template <int P, int DIR, typename T>
+//   FL     : FFT_HALF_IN when elements >= P/2 are zero (registers o >= R1/2
+//            are then not read), FFT_HALF_OUT when only elements < P/2 of the
+//            result are needed (registers o >= R1/2 are then undefined)
+template <int P, int DIR, int FL = FFT_FULL, typename T>
 __device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
 {
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, R2 = Gm::R2, SROW = Gm::SROW;
-    dft_reg<R1, DIR>(v);
+    if (FL & FFT_HALF_IN) dft_reg_halfin<R1, DIR>(v);
+    else dft_reg<R1, DIR>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) {
         cplx<T> w = tw[k1 * G + t];
@@ -138,15 +181,20 @@ __device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const
         for (int s = 0; s < G; ++s) v[i * G + s] = scr[(t + G * i) * SROW + s];
     __syncwarp(gmask);
 #pragma unroll
-    for (int i = 0; i < R2; ++i) dft_reg<G, DIR>(v + i * G);
+    for (int i = 0; i < R2; ++i) {
+        if (FL & FFT_HALF_OUT) dft_reg_halfout<G, DIR>(v + i * G);
+        else dft_reg<G, DIR>(v + i * G);
+    }
     // v[i*G + k2] holds X[t + G*i + R1*k2] = X[t + G*(i + R2*k2)]: reorder to o = i + R2*k2
+    // (with FFT_HALF_OUT only k2 < G/2, i.e. o < R1/2, is defined)
+    constexpr int K2 = (FL & FFT_HALF_OUT) ? G / 2 : G;
     cplx<T> o_[R1];
 #pragma unroll
     for (int i = 0; i < R2; ++i)
 #pragma unroll
-        for (int k2 = 0; k2 < G; ++k2) o_[i + R2 * k2] = v[i * G + k2];
+        for (int k2 = 0; k2 < K2; ++k2) o_[i + R2 * k2] = v[i * G + k2];
 #pragma unroll
-    for (int o = 0; o < R1; ++o) v[o] = o_[o];
+    for (int o = 0; o < R2 * K2; ++o) v[o] = o_[o];
 }
 
 // Mirror values: for each register o (element k = t + G*o) return the value

@@ -141,18 +141,68 @@ __host__ __device__ __forceinline__ size_t fused_smem_bytes(int D, int Dpad, int
     return tw + spec + scr + ms + red;
 }
 
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// One alignment of the constrained relaxation for a cell (reading of the
+// Lagrange-constrained local alignment of Sec. IV): e = b + fictitious field,
+// m' = normalise((1-eta) m + eta e/|e|); accumulates the constraint values
+// and the exact 2x2 Jacobian of C(m'(lambda)) for cells of the window.
+template <typename T> struct RelaxAcc { T C0, C1, J00, J01, J11, res; };
+
+template <typename T>
+__device__ __forceinline__ vec3<T> relax_cell(vec3<T> m, vec3<T> b, bool inW, T dx, T dy, T l0, T l1, T eta,
+                                              RelaxAcc<T> &acc)
+{
+    vec3<T> e = b;
+    if (inW) e.z += l0 * T(2) * m.z * dx + l1 * T(2) * m.z * dy;
+    const T en = dsqrt<T>(e.x * e.x + e.y * e.y + e.z * e.z);
+    const vec3<T> u = {e.x / en, e.y / en, e.z / en};
+    const vec3<T> tq = cross3(m, u);
+    acc.res = max(acc.res, dsqrt<T>(tq.x * tq.x + tq.y * tq.y + tq.z * tq.z));
+    const vec3<T> v = {(T(1) - eta) * m.x + eta * u.x, (T(1) - eta) * m.y + eta * u.y, (T(1) - eta) * m.z + eta * u.z};
+    const T vn = dsqrt<T>(v.x * v.x + v.y * v.y + v.z * v.z);
+    const vec3<T> mp = {v.x / vn, v.y / vn, v.z / vn};
+    if (inW) {
+        const vec3<T> q = {-u.x * u.z / en, -u.y * u.z / en, (T(1) - u.z * u.z) / en};
+        const T mq = mp.x * q.x + mp.y * q.y + mp.z * q.z;
+        const T kap = eta * (q.z - mp.z * mq) / vn;
+        const T w = T(4) * mp.z * m.z * kap;
+        acc.C0 += mp.z * mp.z * dx;
+        acc.C1 += mp.z * mp.z * dy;
+        acc.J00 += w * dx * dx;
+        acc.J01 += w * dx * dy;
+        acc.J11 += w * dy * dy;
+    }
+    return mp;
+}
+
 template <int P, typename T, int MODE, int NT>
 __global__ void __launch_bounds__(NT, 1)
     k_fused(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
             T *__restrict__ accbase, T *__restrict__ outbase, double *__restrict__ red_out,
-            const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base)
+            const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base,
+            RelaxIO *__restrict__ rio, double eta_d, double tol_d, double rc2_d, int max_iter)
 {
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, GPW = Gm::GROUPS_PER_WARP;
     constexpr int NW = NT / 32, NGRP = NT / G;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Replica r_sh;   // the descriptor stays in shared memory, not in registers
     const int ridx = work[blockIdx.x];
-    const Replica r = reps[ridx];
+    if (threadIdx.x == 0) r_sh = reps[ridx];
+    __syncthreads();
+    const Replica &r = r_sh;
     const int D = r.D, Dpad = r.Dpad, DD = D * D;
     const long long cs = (long long)D * RS;           // spectrum component stride
     const long long ms_s = (long long)D * Dpad;       // stage-state component stride
@@ -184,8 +234,20 @@ __global__ void __launch_bounds__(NT, 1)
     const int nrow = row_tasks(D);
     constexpr int ncol = P / 2;
     double esum = 0.0;
-    const long long nst = (MODE == M_FIELD || MODE == M_ENERGY) ? 1 : nsteps;
-    for (long long n = 0; n < nst; ++n) {
+    __shared__ T lam_s[2];
+    __shared__ int conv_s;
+    __shared__ RelaxAcc<T> racc[NW];
+    T relX = 0, relY = 0;
+    if (MODE == M_RELAX) {
+        relX = (T)rio[ridx].X[0];
+        relY = (T)rio[ridx].X[1];
+        if (tid == 0) { lam_s[0] = (T)rio[ridx].lam[0]; lam_s[1] = (T)rio[ridx].lam[1]; conv_s = 0; }
+        __syncthreads();
+    }
+    const long long nst = (MODE == M_FIELD || MODE == M_ENERGY) ? 1 : (MODE == M_RELAX ? (long long)max_iter : nsteps);
+    long long n = 0;
+    T res_last = T(0);
+    for (n = 0; n < nst; ++n) {
         for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
             for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
                 const int q = qb + gw;
@@ -205,6 +267,54 @@ __global__ void __launch_bounds__(NT, 1)
             __syncthreads();
             const T *hr = reinterpret_cast<const T *>(spec);
             const StepParams<T> sp = step_params<T>(r);
+            if (MODE == M_RELAX) {
+                // sweep: trial alignment with the current multipliers, reductions
+                const T eta = (T)eta_d, rc2 = (T)rc2_d, l0 = lam_s[0], l1 = lam_s[1];
+                RelaxAcc<T> a = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                for (int cell = tid; cell < DD; cell += NT) {
+                    if (!r.mask[cell]) continue;
+                    const int y = cell / D, x = cell - y * D;
+                    const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
+                    vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+                    relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, l0, l1, eta, a);
+                }
+                a.C0 = warp_sum_t(a.C0); a.C1 = warp_sum_t(a.C1); a.J00 = warp_sum_t(a.J00);
+                a.J01 = warp_sum_t(a.J01); a.J11 = warp_sum_t(a.J11); a.res = warp_max_t(a.res);
+                if ((tid & 31) == 0) racc[warp] = a;
+                __syncthreads();
+                if (tid == 0) {
+                    RelaxAcc<T> s = racc[0];
+                    for (int w = 1; w < NW; ++w) {
+                        s.C0 += racc[w].C0; s.C1 += racc[w].C1; s.J00 += racc[w].J00; s.J01 += racc[w].J01;
+                        s.J11 += racc[w].J11; s.res = max(s.res, racc[w].res);
+                    }
+                    res_last = s.res;
+                    if (s.res < (T)tol_d) {
+                        conv_s = 1;
+                    } else {
+                        const T det = s.J00 * s.J11 - s.J01 * s.J01;
+                        if (det != T(0) && isfinite(det)) {
+                            lam_s[0] += -(s.J11 * s.C0 - s.J01 * s.C1) / det;
+                            lam_s[1] += -(-s.J01 * s.C0 + s.J00 * s.C1) / det;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (conv_s) break;   // leaves the stage loop; the step loop stops below
+                const T m0 = lam_s[0], m1 = lam_s[1];
+                for (int cell = tid; cell < DD; cell += NT) {
+                    if (!r.mask[cell]) continue;
+                    const int y = cell / D, x = cell - y * D;
+                    const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
+                    vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+                    RelaxAcc<T> dummy = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                    ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, m0, m1, eta, dummy));
+                }
+                __syncthreads();
+                continue;
+            }
             for (int cell = tid; cell < DD; cell += NT) {
                 if (!r.mask[cell]) continue;
                 const int y = cell / D, x = cell - y * D;
@@ -217,6 +327,23 @@ __global__ void __launch_bounds__(NT, 1)
                     epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
             }
             __syncthreads();
+        }
+        if (MODE == M_RELAX && conv_s) break;
+    }
+    if (MODE == M_RELAX) {
+        // the relaxed state back to the caller's buffer
+        for (int cell = tid; cell < DD; cell += NT) {
+            if (!r.mask[cell]) continue;
+            const int y = cell / D, x = cell - y * D;
+            const long long si = (long long)y * Dpad + x;
+            yn.st(si, ms.ld(si));
+        }
+        if (tid == 0) {
+            rio[ridx].lam[0] = (double)lam_s[0];
+            rio[ridx].lam[1] = (double)lam_s[1];
+            rio[ridx].resid = (double)res_last;
+            rio[ridx].iters = (int)n;
+            rio[ridx].status = conv_s ? 0 : 1;
         }
     }
     if (MODE == M_ENERGY) {
@@ -361,7 +488,7 @@ static cudaError_t launch_fused_t(const LaunchArgs &a)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;
     kern<<<a.nwork, NT, a.smem, a.stream>>>(a.reps, a.work, (T *)a.y, (T *)a.acc, (T *)a.out, a.red, (const cplx<T> *)a.tw,
-                                            a.nsteps, a.step_base);
+                                            a.nsteps, a.step_base, a.rio, a.eta, a.tol, a.rc2, a.max_iter);
     return cudaGetLastError();
 }
 
@@ -373,6 +500,7 @@ static cudaError_t launch_fused_p(const LaunchArgs &a)
     case M_ENERGY: return launch_fused_t<P, T, M_ENERGY>(a);
     case M_RK4: return launch_fused_t<P, T, M_RK4>(a);
     case M_HEUN: return launch_fused_t<P, T, M_HEUN>(a);
+    case M_RELAX: return launch_fused_t<P, T, M_RELAX>(a);
     default: return cudaErrorInvalidValue;
     }
 }

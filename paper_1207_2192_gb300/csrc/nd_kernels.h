@@ -8,9 +8,10 @@
 namespace nd {
 
 enum { ND_PREC_FP32 = 0, ND_PREC_FP64 = 1 };
-enum { M_FIELD = 0, M_RK4 = 1, M_HEUN = 2, M_ENERGY = 3 };
+enum { M_FIELD = 0, M_RK4 = 1, M_HEUN = 2, M_ENERGY = 3, M_RELAX = 4 };
 
 struct Replica;
+struct RelaxIO;
 
 struct LaunchArgs {
     int mode = M_FIELD;
@@ -28,6 +29,10 @@ struct LaunchArgs {
     unsigned long long step_base = 0;
     size_t smem = 0;
     cudaStream_t stream = 0;
+    // relaxation
+    RelaxIO *rio = nullptr;          // per replica, indexed like reps
+    double eta = 0.5, tol = 1e-6, rc2 = 0.0;
+    int max_iter = 0;
 };
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im);

@@ -127,7 +127,7 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t smem = fused_smem(P, ND_PREC_FP32, D, Dpad);
-    if (smem == (size_t)-1 || smem > (size_t)optin)
+    if (smem == (size_t)-1 || smem + 1024 > (size_t)optin)
         return fail(ND_ERR_ARG, "nd_step_heun_noalloc: disk too large for the on-chip kernel (diameter above ~60 cells)");
 
     std::lock_guard<std::mutex> lock(g_mu);

@@ -61,9 +61,10 @@ __device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T 
     const int y1 = y0 + 1;
     cplx<T> v[R1];
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
+    for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+    for (int o = 0; o < R1 / 2; ++o) {   // D <= P/2: the upper half is zero padding
         const int x = t + G * o;
-        v[o] = {T(0), T(0)};
         if (active && x < D) {
             if (isxy) {
                 v[o].x = ms[(long long)y0 * ldm + x];
@@ -74,7 +75,7 @@ __device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T 
             }
         }
     }
-    fft_group<P, -1>(v, t, scr, tw, gmask);
+    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
     cplx<T> w[R1];
     mirror_group<P>(v, w, t, lane, gmask);
     if (!active) return;
@@ -134,9 +135,11 @@ __device__ __forceinline__ void col_load(cplx<T> *v, const cplx<T> *col, int D, 
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
+    for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+    for (int o = 0; o < R1 / 2; ++o) {   // rows >= D (and so >= P/2) are zero padding
         const int y = t + G * o;
-        v[o] = (active && y < D) ? col[(long long)y * RS] : cplx<T>{T(0), T(0)};
+        if (active && y < D) v[o] = col[(long long)y * RS];
     }
 }
 
@@ -147,7 +150,7 @@ __device__ __forceinline__ void col_store(const cplx<T> *v, cplx<T> *col, int D,
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
     if (!active) return;
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
+    for (int o = 0; o < R1 / 2; ++o) {
         const int y = t + G * o;
         if (y < D) col[(long long)y * RS] = v[o];
     }
@@ -167,18 +170,18 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
         cplx<T> vx[R1], vy[R1];
         col_load<P>(vx, spec + kx, D, t, active);
         col_load<P>(vy, spec + cstride + kx, D, t, active);
-        fft_group<P, -1>(vx, t, scr, tw, gmask);
-        fft_group<P, -1>(vy, t, scr, tw, gmask);
+        fft_group<P, -1, FFT_HALF_IN>(vx, t, scr, tw, gmask);
+        fft_group<P, -1, FFT_HALF_IN>(vy, t, scr, tw, gmask);
         col_multiply<P>(vx, vy, Ghat, kx, t);
-        fft_group<P, +1>(vx, t, scr, tw, gmask);
-        fft_group<P, +1>(vy, t, scr, tw, gmask);
+        fft_group<P, +1, FFT_HALF_OUT>(vx, t, scr, tw, gmask);
+        fft_group<P, +1, FFT_HALF_OUT>(vy, t, scr, tw, gmask);
         col_store<P>(vx, spec + kx, D, t, active);
         col_store<P>(vy, spec + cstride + kx, D, t, active);
         cplx<T> vz[R1];
         col_load<P>(vz, spec + 2 * cstride + kx, D, t, active);
-        fft_group<P, -1>(vz, t, scr, tw, gmask);
+        fft_group<P, -1, FFT_HALF_IN>(vz, t, scr, tw, gmask);
         col_multiply_z<P>(vz, Ghat, kx, t);
-        fft_group<P, +1>(vz, t, scr, tw, gmask);
+        fft_group<P, +1, FFT_HALF_OUT>(vz, t, scr, tw, gmask);
         col_store<P>(vz, spec + 2 * cstride + kx, D, t, active);
         return;
     }
@@ -188,12 +191,13 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
         cplx<T> *col = spec + c * cstride;
         cplx<T> v[R1];
 #pragma unroll
-        for (int o = 0; o < R1; ++o) {
+        for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+        for (int o = 0; o < R1 / 2; ++o) {
             const int y = t + G * o;
-            v[o] = {T(0), T(0)};
             if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
         }
-        fft_group<P, -1>(v, t, scr, tw, gmask);
+        fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
         cplx<T> w[R1];
         mirror_group<P>(v, w, t, lane, gmask);
 #pragma unroll
@@ -211,10 +215,10 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
             F1 = cscale(F1, s1);
             v[o] = {F0.x - F1.y, F0.y + F1.x};
         }
-        fft_group<P, +1>(v, t, scr, tw, gmask);
+        fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
         if (active) {
 #pragma unroll
-            for (int o = 0; o < R1; ++o) {
+            for (int o = 0; o < R1 / 2; ++o) {
                 const int y = t + G * o;
                 if (y < D) {
                     col[(long long)y * RS] = {v[o].x, T(0)};
@@ -253,11 +257,11 @@ __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> 
         if (!up) { a.y = -a.y; b.y = -b.y; }
         v[o] = {a.x - b.y, a.y + b.x};
     }
-    fft_group<P, +1>(v, t, scr, tw, gmask);
+    fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
     if (!active) return;
     T *oA = reinterpret_cast<T *>(rA), *oB = reinterpret_cast<T *>(rB);
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
+    for (int o = 0; o < R1 / 2; ++o) {
         const int x = t + G * o;
         if (x < D) {
             oA[x] = v[o].x;
