@@ -6,8 +6,8 @@ L = 10 nm, a = 2 nm (50 x 50 cells, 1976 in the disk, FFT grid 128 x 128),
 T = 300 K, alpha = 0.01, dt = 10 fs, Philox seeds 0..255, FP32 fields -- the
 batched Langevin-Heun configuration.  One bench step is CHUNK = 50 stochastic
 Heun time steps of every replica (two full field evaluations each) followed
-by the per-replica observables the statistics need (vortex core position and
-<m>).  A cell-update is one time step of one disk cell of one replica.
+by the per-replica statistics sample (vortex core estimator, FP64 moments and
+uint64 histograms of r and V, all on the device).  A cell-update is one time step of one disk cell of one replica.
 
 Other workloads: "large_disk" (8 replicas of R = 500 nm, L = 20 nm, FFT grid
 1024 x 1024, Heun at 300 K) and "plain" (the batched workload's disk as a
@@ -142,17 +142,20 @@ class Workload:
         self.seeds = np.arange(self.B, dtype=np.uint64)
         self.step = 0
         self.stream = torch.cuda.current_stream()
+        # r histogram: 0.05 nm bins over 0..15 nm; V histogram: 1 m/s bins over 0..400 m/s
+        self.nd.nd_stats_reset(self.h.h, 15e-9, 300, 400.0, 400)
 
     def cell_updates_per_step(self):
         return self.B * self.C * CHUNK
 
     def run_step(self, m=None):
-        """One bench step: CHUNK Heun steps + observables.  Returns launches."""
+        """One bench step: CHUNK Heun steps, then the core statistics sample
+        (core estimator + FP64 moments and uint64 histograms, on the device,
+        no host synchronisation).  Returns the number of kernel launches."""
         target = self.m if m is None else m
         self.h.heun(target, CHUNK, DT, self.T, self.seeds, step0=self.step, stream=self.stream)
         self.step += CHUNK
-        self.h.vortex_core(target, stream=self.stream)
-        self.h.mean_m(target, stream=self.stream)
+        self.nd.nd_stats_sample(self.h.h, target, CHUNK * DT, self.stream)
         return 3
 
 
@@ -188,8 +191,7 @@ def run_ours(args, rank, world, local_rank):
             wl.h.heun(wl.m, CHUNK, DT, wl.T, wl.seeds, step0=wl.step, stream=wl.stream)
             kev[i][1].record()
             wl.step += CHUNK
-            wl.h.vortex_core(wl.m, stream=wl.stream)
-            wl.h.mean_m(wl.m, stream=wl.stream)
+            wl.nd.nd_stats_sample(wl.h.h, wl.m, CHUNK * DT, wl.stream)
             ev[i][1].record()
             launches += 3
         torch.cuda.synchronize()

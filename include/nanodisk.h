@@ -134,8 +134,14 @@ int nd_effective_field(nd_handle *h, const void *m, void *b, void *stream);
 /* Energy of Eq. Hmm for every replica, in units of J = 2AL, evaluated with a
  * double-precision field and double-precision sums whatever the handle's
  * precision: E_out[r] = -{ sum_pairs m_i . m_j + (a^2/lambda^2) sum_i
- * (h_ext + h^M_i / 2) . m_i }.  dEdL_out must be NULL (reserved).
- * E_out is a host array [B]; the call synchronises `stream`. */
+ * (h_ext + h^M_i / 2) . m_i }.  If dEdL_out is not NULL it receives, per
+ * replica, the derivative of the energy in joules, E = J E_out, with respect
+ * to the thickness L at fixed m (J/m): dE/dL = 2A E_out + J d(E/J)/dL, the
+ * second term from the thickness derivative of the Sec. II.B tensor and of
+ * the self factors (always the paper's closed forms).  At a constrained
+ * minimum this is dU/dL by the envelope theorem, which gives dk_F/dL from
+ * two relaxed states (Eq. Ux).  E_out and dEdL_out are host arrays [B]; the
+ * call synchronises `stream`. */
 int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void *stream);
 
 /* n_steps classical RK4 steps of dm/dtau = m x b - alpha m x (m x b)
@@ -186,6 +192,24 @@ int nd_init_vortex(nd_handle *h, void *m, const double *X0, void *stream);
  * may be NULL) is 0 or ND_ERR_NO_VORTEX.  Returns ND_ERR_NO_VORTEX if any
  * replica has none.  Synchronises `stream`. */
 int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, void *stream);
+
+/* Device-resident statistics of the vortex core for the equilibrium checks
+ * of Sec. V.C (radial Boltzmann law Eq. pr, <r^2> = 2kT/k_F, speed law f(V)).
+ * nd_stats_reset allocates and zeroes, per replica, double-precision sums and
+ * two uint64 histograms: r = |r_c| in r_bins bins over [0, r_max) metres and
+ * V in v_bins bins over [0, v_max) m/s.  nd_stats_sample runs the core
+ * estimator of nd_vortex_core on the device state m and accumulates, without
+ * synchronising: samples with a vortex add to n, sum x, sum y, sum r^2 and the
+ * r histogram; two consecutive such samples, dt_sample_seconds apart, add the
+ * speed V = |r_c(t) - r_c(t - dt)|/dt to n_V, sum V^2 and the V histogram;
+ * samples without one count as no_vortex and break the speed chain.
+ * nd_stats_read synchronises `stream` and copies out moments ([B][7]: n,
+ * sum x, sum y, sum r^2, n_V, sum V^2, no_vortex), r_hist ([B][r_bins]) and
+ * v_hist ([B][v_bins]); any output may be NULL. */
+int nd_stats_reset(nd_handle *h, double r_max, int r_bins, double v_max, int v_bins);
+int nd_stats_sample(nd_handle *h, const void *m, double dt_sample_seconds, void *stream);
+int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, unsigned long long *v_hist,
+                  void *stream);
 
 /* Average magnetisation <m> = (1/N) sum_i m_i over each disk (Sec. IV);
  * out is a host array [B][3].  Synchronises `stream`. */

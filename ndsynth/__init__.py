@@ -48,3 +48,9 @@ def sample_cells(D: int, k: int, seed: int = 0) -> np.ndarray:
     """k distinct flat cell indices in [0, D*D) (for sampled checks)."""
     rng = np.random.default_rng(seed)
     return rng.choice(D * D, size=k, replace=False)
+
+
+def sample_indices(n: int, k: int, seed: int = 0) -> np.ndarray:
+    """k distinct indices in [0, n)."""
+    rng = np.random.default_rng(seed)
+    return rng.choice(n, size=k, replace=False)

@@ -59,6 +59,9 @@ SIGNATURES = {
     "nd_vortex_core": (_I, [_P, _P, _P, _P, _P]),
     "nd_mean_m": (_I, [_P, _P, _P, _P]),
     "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
+    "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
+    "nd_stats_sample": (_I, [_P, _P, _D, _P]),
+    "nd_stats_read": (_I, [_P, _P, _P, _P, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
 }
 
@@ -170,10 +173,12 @@ def nd_effective_field(h, m, b, stream=None):
     _check(lib().nd_effective_field(h, _ptr(m), _ptr(b), _stream(stream)))
 
 
-def nd_energy(h, m, nrep, stream=None):
+def nd_energy(h, m, nrep, stream=None, with_dL=False):
+    """Energies in units of J (and dE/dL in J/m when with_dL)."""
     E = np.zeros(nrep)
-    _check(lib().nd_energy(h, _ptr(m), _ptr(E), None, _stream(stream)))
-    return E
+    dL = np.zeros(nrep) if with_dL else None
+    _check(lib().nd_energy(h, _ptr(m), _ptr(E), _ptr(dL), _stream(stream)))
+    return (E, dL) if with_dL else E
 
 
 def nd_step_rk4(h, m, n_steps, dt_seconds, stream=None):
@@ -230,3 +235,19 @@ def nd_step_heun_noalloc(disk, n_replicas, m, n_steps, dt_seconds, T_kelvin, see
     if check:
         _check(rc)
     return rc
+
+
+def nd_stats_reset(h, r_max, r_bins, v_max, v_bins):
+    _check(lib().nd_stats_reset(h, r_max, r_bins, v_max, v_bins))
+
+
+def nd_stats_sample(h, m, dt_sample_seconds, stream=None):
+    _check(lib().nd_stats_sample(h, _ptr(m), dt_sample_seconds, _stream(stream)))
+
+
+def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
+    mom = np.zeros((nrep, 7))
+    hr = np.zeros((nrep, r_bins), dtype=np.uint64)
+    hv = np.zeros((nrep, v_bins), dtype=np.uint64)
+    _check(lib().nd_stats_read(h, _ptr(mom), _ptr(hr), _ptr(hv), _stream(stream)))
+    return mom, hr, hv

@@ -44,6 +44,8 @@ struct DiskInfo {
     unsigned char *mask_d = nullptr;
     double *ghat64 = nullptr;  // [P/2+1][P/2+1][4]
     float *ghat32 = nullptr;
+    double *ghatL = nullptr;   // thickness derivative of the demagnetisation kernel (FP64)
+    double dNx = 0, dNz = 0;   // dN/d(L/a) of the self terms
 };
 
 struct SizeClass {
@@ -108,6 +110,13 @@ struct nd_handle {
     int *aux_i = nullptr;                 // [B * 2]
     RelaxIO *rio_d = nullptr;             // [B] relaxation inputs/outputs
     RelaxIO *rio_h = nullptr;             // pinned [B]
+    // statistics (device resident, filled by nd_stats_sample)
+    StatsAcc *stats = nullptr;
+    unsigned long long *hist_r = nullptr, *hist_v = nullptr;
+    int rbins = 0, vbins = 0;
+    double r_max = 0, v_max = 0;
+    double *core_d = nullptr;             // [B * 4] estimator output of the last sample
+    double *a_rep = nullptr;              // [B] cell edge per replica
     size_t max_smem = 0;
 };
 
@@ -138,8 +147,10 @@ static void upload_reps(nd_handle *h, cudaStream_t st)
     cudaEventRecord(h->slot_ev[h->slot], st);
 }
 
+enum { TAB_MAIN = 0, TAB_DL = 1 };
+
 static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const double *Tk,
-                      const unsigned long long *seed, unsigned long long step0)
+                      const unsigned long long *seed, unsigned long long step0, int table = TAB_MAIN)
 {
     const int B = (int)h->rep_disk.size();
     next_slot(h);
@@ -151,9 +162,9 @@ static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const d
         R.disk = h->rep_disk[r];
         R.state_off = h->rep_off[r];
         R.spec_off = h->rep_spec_off[r];
-        R.Ghat = fp64_kernel ? (const void *)d.ghat64 : (const void *)d.ghat32;
+        R.Ghat = table == TAB_DL ? (const void *)d.ghatL : (fp64_kernel ? (const void *)d.ghat64 : (const void *)d.ghat32);
         R.mask = d.mask_d;
-        for (int k = 0; k < 3; ++k) R.chext[k] = d.cfac * d.h[k];
+        for (int k = 0; k < 3; ++k) R.chext[k] = table == TAB_DL ? 0.0 : d.cfac * d.h[k];
         R.alpha = h->alpha[r];
         R.dtau = d.desc.gamma * d.B0 * dt_seconds;
         double Ts = Tk ? kBoltzmann * Tk[r] / d.J : 0.0;
@@ -284,6 +295,11 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
         const double ro = ds.a / sqrt(M_PI), q = sqrt(ds.L * ds.L + ro * ro);
         di.Nz = (ds.L + ro - q) / ds.L;
         di.Nx = (q - ro) / (2.0 * ds.L);
+        {   // derivatives with respect to l = L/a (lengths in units of a)
+            const double l = ds.L / ds.a, rol = 1.0 / sqrt(M_PI), ql = sqrt(l * l + rol * rol);
+            di.dNz = rol * (rol - ql) / (ql * l * l);
+            di.dNx = rol * (ql - rol) / (2.0 * ql * l * l);
+        }
         for (int k = 0; k < 3; ++k) di.h[k] = ds.hext[k] / ds.Ms;
         di.mask.assign((size_t)di.D * di.D, 0);
         const double rr = (ds.R / ds.a) * (ds.R / ds.a);
@@ -371,6 +387,13 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     if ((e = cudaMalloc(&h->acc, h->elt * h->state_elems)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->rio_d, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMallocHost(&h->rio_h, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMalloc(&h->core_d, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->a_rep, sizeof(double) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    {
+        std::vector<double> av(B);
+        for (int r = 0; r < B; ++r) av[r] = h->disks[h->rep_disk[r]].desc.a;
+        cudaMemcpy(h->a_rep, av.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
+    }
     bool any_global = false, any_global64 = false;
     for (auto &c : h->classes) { any_global |= !c.fused_main; any_global64 |= !c.fused_fp64; }
     if (any_global || any_global64) {
@@ -388,6 +411,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
         cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice);
         if ((e = cudaMalloc(&di.ghat64, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         if ((e = cudaMalloc(&di.ghat32, sizeof(float) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMalloc(&di.ghatL, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     }
     for (int d = 0; d < n_disks; ++d) {
         rc = nd_set_green_tensor(h, d, nullptr);
@@ -401,7 +425,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
 void nd_destroy(nd_handle *h)
 {
     if (!h) return;
-    for (auto &d : h->disks) { cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); }
+    for (auto &d : h->disks) { cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL); }
     for (auto &c : h->classes) cudaFree(c.work_d);
     for (auto &kv : h->tw64) cudaFree(kv.second);
     for (auto &kv : h->tw32) cudaFree(kv.second);
@@ -415,6 +439,11 @@ void nd_destroy(nd_handle *h)
     cudaFree(h->aux_i);
     cudaFree(h->rio_d);
     cudaFreeHost(h->rio_h);
+    cudaFree(h->stats);
+    cudaFree(h->hist_r);
+    cudaFree(h->hist_v);
+    cudaFree(h->core_d);
+    cudaFree(h->a_rep);
     cudaFree(h->acc);
     cudaFree(h->ms);
     cudaFree(h->spec);
@@ -480,6 +509,9 @@ int nd_set_green_tensor(nd_handle *h, int d, const double *Gq)
     }
     cudaError_t e = build_ghat(di.P, di.D, di.desc.L / di.desc.a, di.Nx, di.Nz, di.cfac, gq, di.ghat64, di.ghat32, work, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    // the thickness derivative always follows the paper's closed forms
+    if (e == cudaSuccess) e = build_ghat_dl(di.P, di.D, di.desc.L / di.desc.a, di.dNx, di.dNz, di.cfac, di.ghatL, work, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(work);
     cudaFree(gq);
     if (e != cudaSuccess) return fail(ND_ERR_CUDA, std::string("spectral kernel build: ") + cudaGetErrorString(e));
@@ -513,7 +545,6 @@ int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void
 {
     if (int rc = check_handle(h)) return rc;
     if (!E_out) return fail(ND_ERR_ARG, "null E_out");
-    if (dEdL_out) return fail(ND_ERR_ARG, "dEdL_out is reserved and must be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     void *md = nullptr;
     if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
@@ -530,6 +561,20 @@ int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void
     ND_CUDA(cudaMemcpyAsync(h->red_h, h->red_d, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));
     for (int r = 0; r < B; ++r) E_out[r] = h->red_h[r];
+    if (dEdL_out) {
+        // -1/2 sum_i m_i . (c dh^M/dl)_i with the derivative kernel = d(E/J)/dl at fixed m;
+        // then dE/dL = 2A E/J + J d(E/J)/dl / a  (E = J E/J, J = 2AL)
+        fill_reps(h, true, 0.0, nullptr, nullptr, 0, TAB_DL);
+        upload_reps(h, st);
+        ND_CUDA(cudaMemsetAsync(h->red_d, 0, sizeof(double) * B, st));
+        if (int rc = run_mode(h, M_ENERGY, true, y64, nullptr, 1, st)) return rc;
+        ND_CUDA(cudaMemcpyAsync(h->red_h, h->red_d, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+        ND_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < B; ++r) {
+            const DiskInfo &d = h->disks[h->rep_disk[r]];
+            dEdL_out[r] = 2.0 * d.desc.A * E_out[r] + d.J * h->red_h[r] / d.desc.a;
+        }
+    }
     return ND_OK;
 }
 
@@ -697,6 +742,63 @@ int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, voi
     }
     if (rc) g_err = "no vortex found in at least one replica";
     return rc;
+}
+
+int nd_stats_reset(nd_handle *h, double r_max, int r_bins, double v_max, int v_bins)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!(r_max > 0) || !(v_max > 0) || r_bins < 1 || v_bins < 1) return fail(ND_ERR_ARG, "bad histogram range");
+    const int B = (int)h->rep_disk.size();
+    cudaFree(h->stats); cudaFree(h->hist_r); cudaFree(h->hist_v);
+    h->stats = nullptr; h->hist_r = h->hist_v = nullptr;
+    ND_CUDA(cudaMalloc(&h->stats, sizeof(StatsAcc) * B));
+    ND_CUDA(cudaMalloc(&h->hist_r, sizeof(unsigned long long) * B * r_bins));
+    ND_CUDA(cudaMalloc(&h->hist_v, sizeof(unsigned long long) * B * v_bins));
+    ND_CUDA(cudaMemset(h->stats, 0, sizeof(StatsAcc) * B));
+    ND_CUDA(cudaMemset(h->hist_r, 0, sizeof(unsigned long long) * B * r_bins));
+    ND_CUDA(cudaMemset(h->hist_v, 0, sizeof(unsigned long long) * B * v_bins));
+    h->rbins = r_bins; h->vbins = v_bins; h->r_max = r_max; h->v_max = v_max;
+    return ND_OK;
+}
+
+int nd_stats_sample(nd_handle *h, const void *m, double dt_sample_seconds, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->stats) return fail(ND_ERR_ARG, "call nd_stats_reset first");
+    if (!(dt_sample_seconds > 0)) return fail(ND_ERR_ARG, "dt_sample must be positive");
+    if (!m || !is_device_ptr(m)) return fail(ND_ERR_ARG, "nd_stats_sample needs a device state");
+    cudaStream_t st = (cudaStream_t)stream;
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        const double rcut = 4.0 * d.lambda / d.desc.a;
+        ND_CUDA(launch_vortex_core(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d,
+                                   (int)c.reps.size(), m, rcut * rcut, h->core_d, st));
+        ND_CUDA(launch_stats_update(c.work_d, (int)c.reps.size(), h->core_d, h->a_rep, h->stats, h->hist_r, h->hist_v,
+                                    h->rbins, h->vbins, h->r_max, h->v_max, dt_sample_seconds, st));
+    }
+    return ND_OK;
+}
+
+int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, unsigned long long *v_hist, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->stats) return fail(ND_ERR_ARG, "call nd_stats_reset first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = (int)h->rep_disk.size();
+    ND_CUDA(cudaStreamSynchronize(st));
+    std::vector<StatsAcc> s(B);
+    ND_CUDA(cudaMemcpy(s.data(), h->stats, sizeof(StatsAcc) * B, cudaMemcpyDeviceToHost));
+    if (moments)
+        for (int r = 0; r < B; ++r) {
+            double *o = moments + 7 * r;
+            o[0] = s[r].n; o[1] = s[r].sx; o[2] = s[r].sy; o[3] = s[r].sr2;
+            o[4] = s[r].nv; o[5] = s[r].sv2; o[6] = s[r].no_vortex;
+        }
+    if (r_hist) ND_CUDA(cudaMemcpy(r_hist, h->hist_r, sizeof(unsigned long long) * B * h->rbins, cudaMemcpyDeviceToHost));
+    if (v_hist) ND_CUDA(cudaMemcpy(v_hist, h->hist_v, sizeof(unsigned long long) * B * h->vbins, cudaMemcpyDeviceToHost));
+    return ND_OK;
 }
 
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream)

@@ -34,6 +34,35 @@ __global__ void k_green_quarter(int D, double l, double Nx, double Nz, double *G
     }
 }
 
+// Thickness derivative of the table above, d(a^2 G)/dl at fixed displacement
+// (lengths in units of a), and of the self terms:
+//   dN_z/dl = r_o (r_o - q)/(q l^2),  dN_x/dl = r_o (q - r_o)/(2 q l^2),  q = sqrt(l^2 + r_o^2).
+__global__ void k_green_quarter_dl(int D, double l, double dNx, double dNz, double *Gq)
+{
+    const int n = D * D;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int dy = i / D, dx = i - dy * D;
+        double xx, yy, xy, zz;
+        if (dx == 0 && dy == 0) {
+            xx = -dNx; yy = -dNx; xy = 0.0; zz = -dNz;
+        } else {
+            const double x = dx, y = dy, r2 = x * x + y * y, r = sqrt(r2), s = sqrt(r2 + l * l);
+            const double ds = l / s, r4 = r2 * r2;
+            // G_xx = l/(2 pi r^4) (x^2/s - y^2/(s+r))
+            xx = (1.0 / (2.0 * M_PI * r4)) * ((x * x / s - y * y / (s + r)) + l * (-x * x * ds / (s * s) + y * y * ds / ((s + r) * (s + r))));
+            yy = (1.0 / (2.0 * M_PI * r4)) * ((y * y / s - x * x / (s + r)) + l * (-y * y * ds / (s * s) + x * x * ds / ((s + r) * (s + r))));
+            // G_xy = g(l) x y / (2 pi r^4), g = l (2s+r)/((s+r) s)
+            const double den = (s + r) * s;
+            const double g = (2.0 * s + r) / den + l * ds * (2.0 * (s + r) * s - (2.0 * s + r) * (2.0 * s + r)) / (den * den);
+            xy = g * x * y / (2.0 * M_PI * r4);
+            // G_zz = -f(l)/(2 pi r), f = l/(s (s+r))
+            const double f = (s * (s + r) - l * ds * (2.0 * s + r)) / (den * den);
+            zz = -f / (2.0 * M_PI * r);
+        }
+        Gq[i] = xx; Gq[n + i] = yy; Gq[2 * n + i] = xy; Gq[3 * n + i] = zz;
+    }
+}
+
 __global__ void k_trig_table(int P, double *cs)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
@@ -66,7 +95,8 @@ __global__ void k_ghat_pass1(int P, int D, const double *Gq, const double *cs, d
 //   Ghat_c = s_c sum_dy w(dy) T1[c][dy][kx] f_c(2 pi ky dy / P), s_xy = -1,
 //   diagonal: (c Ghat + 2 cos(2 pi kx/P) + 2 cos(2 pi ky/P)) / P^2 (exchange folded in),
 //   xy:       c Ghat_xy / P^2.
-__global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const double *cs, double *G64, float *G32)
+__global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const double *cs, double *G64, float *G32,
+                             int with_exchange)
 {
     const int KH = P / 2 + 1, n = KH * KH;
     const double inv = 1.0 / ((double)P * (double)P);
@@ -83,7 +113,7 @@ __global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const 
             }
             v[c] = (c == 2) ? -acc : acc;
         }
-        const double kex = 2.0 * cs[2 * kx] + 2.0 * cs[2 * ky];
+        const double kex = with_exchange ? 2.0 * cs[2 * kx] + 2.0 * cs[2 * ky] : 0.0;
         const double o[4] = {(cfac * v[0] + kex) * inv, (cfac * v[1] + kex) * inv, cfac * v[2] * inv,
                              (cfac * v[3] + kex) * inv};
         for (int c = 0; c < 4; ++c) {
@@ -108,7 +138,19 @@ cudaError_t build_ghat(int P, int D, double l, double Nx, double Nz, double cfac
     k_trig_table<<<(P + 255) / 256, 256, 0, st>>>(P, cs);
     const int KH = P / 2 + 1;
     k_ghat_pass1<<<(4 * D * KH + 255) / 256, 256, 0, st>>>(P, D, Gq, cs, T1);
-    k_ghat_pass2<<<(KH * KH + 127) / 128, 128, 0, st>>>(P, D, cfac, T1, cs, G64, G32);
+    k_ghat_pass2<<<(KH * KH + 127) / 128, 128, 0, st>>>(P, D, cfac, T1, cs, G64, G32, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t build_ghat_dl(int P, int D, double l, double dNx, double dNz, double cfac, double *GL64, double *work,
+                          cudaStream_t st)
+{
+    double *Gq = work, *T1 = Gq + (size_t)4 * D * D, *cs = T1 + (size_t)4 * D * (P / 2 + 1);
+    k_green_quarter_dl<<<(D * D + 255) / 256, 256, 0, st>>>(D, l, dNx, dNz, Gq);
+    k_trig_table<<<(P + 255) / 256, 256, 0, st>>>(P, cs);
+    const int KH = P / 2 + 1;
+    k_ghat_pass1<<<(4 * D * KH + 255) / 256, 256, 0, st>>>(P, D, Gq, cs, T1);
+    k_ghat_pass2<<<(KH * KH + 127) / 128, 128, 0, st>>>(P, D, cfac, T1, cs, GL64, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -253,6 +295,50 @@ cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, i
 {
     if (prec == ND_PREC_FP64) k_vortex_core<double><<<nwork, 256, 0, st>>>(reps, work, (const double *)y, rc2, out);
     else k_vortex_core<float><<<nwork, 256, 0, st>>>(reps, work, (const float *)y, rc2, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ statistics
+
+// Per-replica accumulation of the core statistics of Sec. V.C in double
+// precision with 64-bit histogram counts: samples where a vortex was found
+// add r = |r_c| to <x>, <y>, <r^2> and to the r histogram; consecutive found
+// samples add the speed V = |r_c(t) - r_c(t - dt)|/dt to <V^2> and the V
+// histogram.  One thread per replica; core holds the estimator output in
+// cell units ([4] per replica: x, y, status, plaquette).
+__global__ void k_stats_update(const int *work, int nwork, const double *core, const double *a_of_rep,
+                               StatsAcc *st, unsigned long long *hr, unsigned long long *hv, int rb, int vb,
+                               double r_max, double v_max, double dt)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    const int r = work[w];
+    const double *c = core + 4 * r;
+    StatsAcc &S = st[r];
+    if (c[2] != 0.0) {
+        S.no_vortex += 1.0;
+        S.have_prev = 0;
+        return;
+    }
+    const double a = a_of_rep[r];
+    const double x = c[0] * a, y = c[1] * a, rr = sqrt(x * x + y * y);
+    S.n += 1.0; S.sx += x; S.sy += y; S.sr2 += x * x + y * y;
+    const long long br = (long long)floor(rr / r_max * rb);
+    if (br >= 0 && br < rb) hr[(size_t)r * rb + br] += 1ull;
+    if (S.have_prev) {
+        const double vx = (x - S.px) / dt, vy = (y - S.py) / dt, v = sqrt(vx * vx + vy * vy);
+        S.nv += 1.0; S.sv2 += v * v;
+        const long long bv = (long long)floor(v / v_max * vb);
+        if (bv >= 0 && bv < vb) hv[(size_t)r * vb + bv] += 1ull;
+    }
+    S.px = x; S.py = y; S.have_prev = 1;
+}
+
+cudaError_t launch_stats_update(const int *work, int nwork, const double *core, const double *a_of_rep, StatsAcc *st,
+                                unsigned long long *hr, unsigned long long *hv, int rb, int vb, double r_max,
+                                double v_max, double dt, cudaStream_t s)
+{
+    k_stats_update<<<(nwork + 127) / 128, 128, 0, s>>>(work, nwork, core, a_of_rep, st, hr, hv, rb, vb, r_max, v_max, dt);
     return cudaGetLastError();
 }
 

@@ -120,6 +120,15 @@ struct RelaxIO {
     int status;       // 0 converged, 1 max_iter reached
 };
 
+// Per-replica statistics accumulators (double precision sums).
+struct StatsAcc {
+    double n, sx, sy, sr2;   // samples with a vortex, sums of x, y, x^2 + y^2 (metres)
+    double nv, sv2;          // speed samples and the sum of V^2 (m^2/s^2)
+    double no_vortex;        // samples without a vortex
+    double px, py;           // previous core position
+    int have_prev, pad;
+};
+
 // Status word written by kernels (bit flags), read by the host after a sync.
 enum : unsigned { ND_DEV_NAN = 1u, ND_DEV_TIMEOUT = 2u };
 

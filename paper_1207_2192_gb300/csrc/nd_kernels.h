@@ -12,6 +12,7 @@ enum { M_FIELD = 0, M_RK4 = 1, M_HEUN = 2, M_ENERGY = 3, M_RELAX = 4 };
 
 struct Replica;
 struct RelaxIO;
+struct StatsAcc;
 
 struct LaunchArgs {
     int mode = M_FIELD;
@@ -48,6 +49,9 @@ size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] 
 cudaError_t build_ghat(int P, int D, double L_over_a, double Nx, double Nz, double c, const double *Gq_dev,
                        double *Ghat64, float *Ghat32, double *work, cudaStream_t st);
 size_t build_ghat_work_doubles(int P, int D);
+// Spectral kernel of c d(a^2 G)/dl (l = L/a, no exchange), same layout and 1/P^2 scale.
+cudaError_t build_ghat_dl(int P, int D, double l, double dNx, double dNz, double cfac, double *GL64, double *work,
+                          cudaStream_t st);
 
 // Auxiliary kernels (nd_aux.cu).
 cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, int nwork, int maxD, void *y,
@@ -56,6 +60,9 @@ cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, i
 cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, const void *y,
                                double rc2, double *out /*[nrep][4]: xc, yc (units of a), status, pad*/,
                                cudaStream_t st);
+cudaError_t launch_stats_update(const int *work, int nwork, const double *core, const double *a_of_rep, StatsAcc *st,
+                                unsigned long long *hr, unsigned long long *hv, int rb, int vb, double r_max,
+                                double v_max, double dt, cudaStream_t s);
 cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y,
                           double *out /*[nrep][3]*/, cudaStream_t st);
 cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st);

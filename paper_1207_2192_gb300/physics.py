@@ -1,0 +1,58 @@
+"""Host-side analysis on top of the library calls: the force constant k_F
+from constrained relaxations (Eq. Ux), its thickness derivative by the
+envelope theorem, the gyrotropic frequency from a core trajectory, and the
+Thiele relation (Eq. OG).  The field, relaxations and energies run in the
+CUDA library; this module only fits numbers."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from ._binding import ND_ERR_NOT_CONVERGED, ND_OK, nd_energy
+
+
+def kF_map(h, xs, tol=1e-6, max_iter=40000, stream=None):
+    """Relax one replica per core position x (along x, metres) of a
+    single-disk handle with len(xs) replicas and fit U(x) = U(0) + kF x^2/2.
+
+    Returns dict with U (J units), U_J (joules), kF_fit (N/m, least squares
+    over x^2 with the x = 0 point), kF_2pt (from the first nonzero x),
+    dkF_dL (N/m^2, envelope theorem on the same two states), lam, iters.
+    """
+    xs = np.asarray(xs, dtype=np.float64)
+    assert h.B == len(xs) and xs[0] == 0.0
+    X = np.stack([xs, np.zeros_like(xs)], 1)
+    m = h.empty_device()
+    h.init_vortex(m, X)
+    rc, U, lam, it = h.relax(m, X, tol=tol, max_iter=max_iter, stream=stream)
+    if rc not in (ND_OK, ND_ERR_NOT_CONVERGED):
+        raise RuntimeError(f"relaxation failed ({rc})")
+    E, dEdL = nd_energy(h.h, m, h.B, stream, with_dL=True)
+    J = h.units[0][4]
+    UJ = E * J
+    A = np.stack([np.ones_like(xs), 0.5 * xs ** 2], 1)
+    coef, *_ = np.linalg.lstsq(A, UJ, rcond=None)
+    x1 = xs[1]
+    kF_2pt = 2.0 * (UJ[1] - UJ[0]) / x1 ** 2
+    dkF_dL = 2.0 * (dEdL[1] - dEdL[0]) / x1 ** 2
+    return dict(U=E, U_J=UJ, kF_fit=coef[1], kF_2pt=kF_2pt, dkF_dL=dkF_dL, dEdL=dEdL, lam=lam, iters=it,
+                converged=(rc == ND_OK), state=m)
+
+
+def dkF_d_aspect(dkF_dL, R):
+    """d kF / d(L/R) at fixed radius and mask: R dkF/dL."""
+    return R * dkF_dL
+
+
+def omega_from_core(xc, yc, dtau):
+    """Dimensionless angular frequency of gyrotropic motion: slope of the
+    unwrapped polar angle of the core position against tau (least squares)."""
+    phi = np.unwrap(np.arctan2(np.asarray(yc), np.asarray(xc)))
+    t = np.arange(len(phi)) * dtau
+    return np.polyfit(t, phi, 1)[0]
+
+
+def omega_thiele(kF, a, L, A, Q=1):
+    """Omega_G = -kF a^2 / (4 pi L A Q) (Eq. OG)."""
+    return -kF * a * a / (4.0 * math.pi * L * A * Q)
