@@ -147,7 +147,9 @@ int nd_energy(nd_handle *h, const void *m, double *E_out, double *dEdL_out, void
 /* n_steps classical RK4 steps of dm/dtau = m x b - alpha m x (m x b)
  * (Sec. III.A) for every replica, with the full field at all four stages
  * and |m_i| = 1 restored after each step; dtau = gamma B0 dt_seconds.
- * m is updated in place. */
+ * m is updated in place.  With more replicas than resident CTAs the steps
+ * are spread evenly over one CTA per SM, replicas changing CTA between steps
+ * (a cooperative launch; see nd_check_status). */
 int nd_step_rk4(nd_handle *h, void *m, long long n_steps, double dt_seconds, void *stream);
 
 /* n_steps stochastic Heun steps of the Langevin equation (Eq. LV, Sec.
@@ -179,6 +181,13 @@ int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, co
  * ND_ERR_NOT_CONVERGED if a replica reached max_iter.  Synchronises `stream`. */
 int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int max_iter, double *U_out,
                          double *lambda_out, int *iters_out, void *stream);
+
+/* Synchronise `stream` and read (then clear) the handle's device status
+ * word.  Returns ND_ERR_TIMEOUT if a bounded device-side wait expired since
+ * the last check (the time-sliced stepping schedule hands replicas between
+ * CTAs through flags and gives up rather than hang), ND_ERR_NAN if a kernel
+ * flagged non-finite values, else ND_OK.  The paper has no counterpart. */
+int nd_check_status(nd_handle *h, void *stream);
 
 /* Analytic q = +1 vortex centred at X0[r] = (x0, y0) metres (host array
  * [B][2]) for every replica (Sec. IV profile): in-plane angle atan2(y - y0,

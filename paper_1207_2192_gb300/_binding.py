@@ -60,6 +60,7 @@ SIGNATURES = {
     "nd_mean_m": (_I, [_P, _P, _P, _P]),
     "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
     "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
+    "nd_check_status": (_I, [_P, _P]),
     "nd_stats_sample": (_I, [_P, _P, _D, _P]),
     "nd_stats_read": (_I, [_P, _P, _P, _P, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
@@ -251,3 +252,8 @@ def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
     hv = np.zeros((nrep, v_bins), dtype=np.uint64)
     _check(lib().nd_stats_read(h, _ptr(mom), _ptr(hr), _ptr(hv), _stream(stream)))
     return mom, hr, hv
+
+
+def nd_check_status(h, stream=None):
+    """Synchronise and return the device status code (ND_OK, ND_ERR_TIMEOUT, ND_ERR_NAN)."""
+    return lib().nd_check_status(h, _stream(stream))

@@ -55,6 +55,12 @@ struct SizeClass {
     bool fused_main = false;   // fused kernel in the handle precision
     bool fused_fp64 = false;   // fused kernel in FP64 (energy)
     size_t smem_main = 0, smem_fp64 = 0;
+    size_t smem_wbuf = 0;      // fused Heun with the normals kept in shared memory (0: does not fit)
+    // time-sliced schedule, cached per (mode, n_steps)
+    SegmentHost *segs_d = nullptr;
+    int *seg_off_d = nullptr;
+    int seg_mode = -1, seg_ncta = 0;
+    long long seg_nsteps = -1;
 };
 
 int next_pow2_at_least(int n)
@@ -118,11 +124,16 @@ struct nd_handle {
     double *core_d = nullptr;             // [B * 4] estimator output of the last sample
     double *a_rep = nullptr;              // [B] cell edge per replica
     size_t max_smem = 0;
+    int n_sm = 0;
+    int *flags_d = nullptr;               // [B] replica hand-over flags of the time-sliced schedule
+    unsigned *status_d = nullptr;         // device status word (ND_DEV_* bits)
 };
 
 static int setup_class_paths(nd_handle *h)
 {
     for (auto &c : h->classes) {
+        const size_t w = fused_smem(c.P, h->prec, c.maxD, c.maxDpad, true);
+        c.smem_wbuf = (w != (size_t)-1 && w + 1024 <= h->max_smem) ? w : 0;
         // 1 KiB of the per-block limit is left for the kernels' static shared variables
         c.smem_main = fused_smem(c.P, h->prec, c.maxD, c.maxDpad);
         c.fused_main = c.smem_main != (size_t)-1 && c.smem_main + 1024 <= h->max_smem;
@@ -179,6 +190,34 @@ static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const d
     }
 }
 
+// Time-sliced schedule for more replicas than resident CTAs: the class's
+// replica-steps (B_c x n) are cut into ncta equal, contiguous ranges; CTA i
+// runs the start of the replica it shares with CTA i+1 first (and flags it),
+// then its whole replicas, then the end of the replica it shares with CTA i-1
+// after waiting for that flag.  Every CTA does the same number of steps.
+static void build_segments(int Bc, long long n, int ncta, std::vector<SegmentHost> &segs, std::vector<int> &off)
+{
+    const long long W = (long long)Bc * n, s = (W + ncta - 1) / ncta;
+    segs.clear();
+    off.assign(ncta + 1, 0);
+    for (int i = 0; i < ncta; ++i) {
+        off[i] = (int)segs.size();
+        const long long start = (long long)i * s, end = std::min(W, start + s);
+        if (start >= end) continue;
+        const int r0 = (int)(start / n), r1 = (int)((end - 1) / n);
+        const long long o0 = start % n, o1 = (end - 1) % n + 1;
+        if (r0 == r1) {
+            segs.push_back({r0, o0 > 0 ? 1 : 0, o1 < n ? 1 : 0, 0, o0, o1 - o0});
+            continue;
+        }
+        if (o1 < n) segs.push_back({r1, 0, 1, 0, 0, o1});             // start of the replica continued by CTA i+1
+        for (int r = (o0 > 0 ? r0 + 1 : r0); r < r1; ++r) segs.push_back({r, 0, 0, 0, 0, n});
+        if (o1 == n) segs.push_back({r1, 0, 0, 0, 0, n});
+        if (o0 > 0) segs.push_back({r0, 1, 0, 0, o0, n - o0});          // end of the replica started by CTA i-1
+    }
+    off[ncta] = (int)segs.size();
+}
+
 // Run one mode over all replicas.  fp64 selects the FP64 kernels (with y a
 // double buffer of the state layout), otherwise the handle precision.
 static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st)
@@ -201,6 +240,41 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
         if (fused) {
             a.smem = fp64 ? c.smem_fp64 : c.smem_main;
+            a.status = h->status_d;
+            if (mode == M_HEUN && !fp64 && c.smem_wbuf) {
+                a.smem = c.smem_wbuf;
+                a.use_wbuf = 1;
+            }
+            if ((mode == M_HEUN || mode == M_RK4) && !fp64 && nsteps >= 2) {
+                // localise the replicas' indices to the class: segments refer to positions in c.reps
+                const int per_sm = fused_blocks_per_sm(c.P, prec, mode, a.smem);
+                const int ncta = per_sm * h->n_sm;
+                const int Bc = (int)c.reps.size();
+                if (per_sm > 0 && Bc > ncta) {
+                    if (c.seg_mode != mode || c.seg_nsteps != nsteps || c.seg_ncta != ncta) {
+                        std::vector<SegmentHost> segs;
+                        std::vector<int> off;
+                        build_segments(Bc, nsteps, ncta, segs, off);
+                        for (auto &g : segs) g.rep = c.reps[g.rep];
+                        cudaFree(c.segs_d);
+                        cudaFree(c.seg_off_d);
+                        c.segs_d = nullptr;
+                        c.seg_off_d = nullptr;
+                        ND_CUDA(cudaMalloc(&c.segs_d, sizeof(SegmentHost) * segs.size()));
+                        ND_CUDA(cudaMalloc(&c.seg_off_d, sizeof(int) * off.size()));
+                        ND_CUDA(cudaMemcpy(c.segs_d, segs.data(), sizeof(SegmentHost) * segs.size(), cudaMemcpyHostToDevice));
+                        ND_CUDA(cudaMemcpy(c.seg_off_d, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+                        c.seg_mode = mode;
+                        c.seg_nsteps = nsteps;
+                        c.seg_ncta = ncta;
+                    }
+                    ND_CUDA(cudaMemsetAsync(h->flags_d, 0, sizeof(int) * h->rep_disk.size(), st));
+                    a.segs = c.segs_d;
+                    a.seg_off = c.seg_off_d;
+                    a.flags = h->flags_d;
+                    a.ncta = ncta;
+                }
+            }
             ND_CUDA(launch_fused(c.P, prec, a));
         } else {
             a.ms = fp64 ? (void *)h->ms64 : h->ms;
@@ -267,6 +341,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     h->max_smem = (size_t)optin;
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
     // twiddle constants exp(-2 pi i k / 32)
     {
         double re[32], im[32];
@@ -386,6 +461,9 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     if ((e = cudaMalloc(&h->aux_i, sizeof(int) * 2 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->acc, h->elt * h->state_elems)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->rio_d, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->flags_d, sizeof(int) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->status_d, sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemset(h->status_d, 0, sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
     if ((e = cudaMallocHost(&h->rio_h, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
     if ((e = cudaMalloc(&h->core_d, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->a_rep, sizeof(double) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -426,7 +504,9 @@ void nd_destroy(nd_handle *h)
 {
     if (!h) return;
     for (auto &d : h->disks) { cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL); }
-    for (auto &c : h->classes) cudaFree(c.work_d);
+    for (auto &c : h->classes) { cudaFree(c.work_d); cudaFree(c.segs_d); cudaFree(c.seg_off_d); }
+    cudaFree(h->flags_d);
+    cudaFree(h->status_d);
     for (auto &kv : h->tw64) cudaFree(kv.second);
     for (auto &kv : h->tw32) cudaFree(kv.second);
     for (int k = 0; k < nd_handle::kSlots; ++k)
@@ -742,6 +822,19 @@ int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, voi
     }
     if (rc) g_err = "no vortex found in at least one replica";
     return rc;
+}
+
+int nd_check_status(nd_handle *h, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    ND_CUDA(cudaStreamSynchronize(st));
+    unsigned v = 0;
+    ND_CUDA(cudaMemcpy(&v, h->status_d, sizeof(v), cudaMemcpyDeviceToHost));
+    ND_CUDA(cudaMemset(h->status_d, 0, sizeof(v)));
+    if (v & ND_DEV_TIMEOUT) return fail(ND_ERR_TIMEOUT, "a bounded device-side wait expired (replica hand-over)");
+    if (v & ND_DEV_NAN) return fail(ND_ERR_NAN, "non-finite values in the state");
+    return ND_OK;
 }
 
 int nd_stats_reset(nd_handle *h, double r_max, int r_bins, double v_max, int v_bins)

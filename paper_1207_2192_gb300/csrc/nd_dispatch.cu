@@ -7,8 +7,10 @@ cudaError_t upload_tw_fused_f32(const double *, const double *);
 cudaError_t upload_tw_fused_f64(const double *, const double *);
 cudaError_t upload_tw_glob_f32(const double *, const double *);
 cudaError_t upload_tw_glob_f64(const double *, const double *);
-size_t fused_smem_f32(int P, int D, int Dpad);
-size_t fused_smem_f64(int P, int D, int Dpad);
+size_t fused_smem_f32(int P, int D, int Dpad, bool wbuf);
+size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf);
+int fused_blocks_per_sm_f32(int P, int mode, size_t smem);
+int fused_blocks_per_sm_f64(int P, int mode, size_t smem);
 cudaError_t launch_fused_f32(int P, const LaunchArgs &a);
 cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
 cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
@@ -23,9 +25,14 @@ cudaError_t upload_twiddle_constants(const double *re, const double *im)
     return upload_tw_glob_f64(re, im);
 }
 
-size_t fused_smem(int P, int prec, int D, int Dpad)
+size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf)
 {
-    return prec == ND_PREC_FP64 ? fused_smem_f64(P, D, Dpad) : fused_smem_f32(P, D, Dpad);
+    return prec == ND_PREC_FP64 ? fused_smem_f64(P, D, Dpad, wbuf) : fused_smem_f32(P, D, Dpad, wbuf);
+}
+
+int fused_blocks_per_sm(int P, int prec, int mode, size_t smem)
+{
+    return prec == ND_PREC_FP64 ? fused_blocks_per_sm_f64(P, mode, smem) : fused_blocks_per_sm_f32(P, mode, smem);
 }
 
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a)

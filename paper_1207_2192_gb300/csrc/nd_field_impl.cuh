@@ -60,10 +60,12 @@ template <typename T> struct V3Ptr {
 //   yn  : state y_n (user buffer), acc : stage accumulator (scratch)
 //   b   : the full dimensionless induction b_i at this cell
 // Returns the cell's contribution to the reduced quantity (energy mode).
+// For Heun, wbuf (when not null) keeps the predictor's normals for the
+// corrector, which then reads them instead of regenerating them.
 template <typename T, int MODE>
 __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long long si, long long mi, vec3<T> b,
                                                 V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
-                                                unsigned long long step)
+                                                unsigned long long step, V3Ptr<T> wbuf = V3Ptr<T>{nullptr, 0})
 {
     const StepParams<T> sp = step_params<T>(r);
     const T alpha = sp.alpha, dt = sp.dtau;
@@ -97,7 +99,13 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
         const T sig = sp.sigma;
         vec3<T> g = {b.x * dt, b.y * dt, b.z * dt};
         if (r.flags & 1) {
-            vec3<T> w = thermal_normals<T>(r.seed, (uint32_t)cell, step);
+            vec3<T> w;
+            if (wbuf.p && stage == 1) {
+                w = wbuf.ld(mi);
+            } else {
+                w = thermal_normals<T>(r.seed, (uint32_t)cell, step);
+                if (wbuf.p) wbuf.st(mi, w);
+            }
             g.x += sig * w.x; g.y += sig * w.y; g.z += sig * w.z;
         }
         vec3<T> d = heun_dm(m, g, alpha);
@@ -130,7 +138,7 @@ __device__ __forceinline__ double warp_sum(double v)
 // ------------------------------------------------------------ fused path
 
 template <int P, typename T>
-__host__ __device__ __forceinline__ size_t fused_smem_bytes(int D, int Dpad, int nthreads)
+__host__ __device__ __forceinline__ size_t fused_smem_bytes(int D, int Dpad, int nthreads, bool wbuf = false)
 {
     using Gm = FFTGeom<P>;
     size_t tw = sizeof(cplx<T>) * Gm::R1 * Gm::G;
@@ -138,7 +146,32 @@ __host__ __device__ __forceinline__ size_t fused_smem_bytes(int D, int Dpad, int
     size_t scr = sizeof(cplx<T>) * (size_t)(nthreads / Gm::G) * Gm::SCRATCH;
     size_t ms = sizeof(T) * 3 * (size_t)D * Dpad;
     size_t red = sizeof(double) * 32;
-    return tw + spec + scr + ms + red;
+    size_t w = wbuf ? sizeof(T) * 3 * (size_t)D * Dpad : 0;
+    return tw + spec + scr + ms + red + w;
+}
+
+// A piece of one replica's trajectory run by one CTA (time-sliced schedule).
+struct Segment {
+    int rep;                 // replica index
+    int wait;                // wait until flags[rep] is set before starting
+    int signal;              // set flags[rep] when done
+    int pad;
+    long long step_begin;    // first time step (relative to the call's step0)
+    long long nsteps;
+};
+
+// Bounded wait of thread 0 on a flag set by another CTA of the same
+// (cooperative) launch; returns false after about 2^22 polls.
+__device__ __forceinline__ bool wait_flag(int *flag)
+{
+    for (long long it = 0; it < (1LL << 22); ++it) {
+        if (atomicAdd(flag, 0) != 0) {
+            __threadfence();
+            return true;
+        }
+        __nanosleep(256);
+    }
+    return false;
 }
 
 template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
@@ -192,168 +225,193 @@ __global__ void __launch_bounds__(NT, 1)
     k_fused(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
             T *__restrict__ accbase, T *__restrict__ outbase, double *__restrict__ red_out,
             const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base,
-            RelaxIO *__restrict__ rio, double eta_d, double tol_d, double rc2_d, int max_iter)
+            RelaxIO *__restrict__ rio, double eta_d, double tol_d, double rc2_d, int max_iter,
+            const Segment *__restrict__ segs, const int *__restrict__ seg_off, int *__restrict__ flags,
+            unsigned *__restrict__ status, int use_wbuf)
 {
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, GPW = Gm::GROUPS_PER_WARP;
     constexpr int NW = NT / 32, NGRP = NT / G;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Replica r_sh;   // the descriptor stays in shared memory, not in registers
-    const int ridx = work[blockIdx.x];
-    if (threadIdx.x == 0) r_sh = reps[ridx];
-    __syncthreads();
-    const Replica &r = r_sh;
-    const int D = r.D, Dpad = r.Dpad, DD = D * D;
-    const long long cs = (long long)D * RS;           // spectrum component stride
-    const long long ms_s = (long long)D * Dpad;       // stage-state component stride
-
-    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
-    cplx<T> *spec = tw + R1 * G;
-    cplx<T> *scratch = spec + 3 * cs;
-    T *msm = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);
-    double *red = reinterpret_cast<double *>(msm + 3 * ms_s);
-
+    __shared__ T lam_s[2];
+    __shared__ int conv_s, ok_s;
+    __shared__ RelaxAcc<T> racc[NW];
     const int tid = threadIdx.x, warp = tid >> 5;
     GroupId<P> gid(tid);
-    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
     const int gw = gid.group % GPW;
-
-    load_twiddles<P>(tw, twP, tid, NT);
-    V3Ptr<T> yn{ybase + r.state_off, ms_s};
-    V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s};
-    V3Ptr<T> out{outbase ? outbase + r.state_off : nullptr, ms_s};
-    V3Ptr<T> ms{msm, ms_s};
-    for (int cell = tid; cell < DD; cell += NT) {
-        const int y = cell / D, x = cell - y * D;
-        const long long si = (long long)y * Dpad + x;
-        vec3<T> v = r.mask[cell] ? yn.ld(si) : vec3<T>{T(0), T(0), T(0)};
-        ms.st(si, v);
-    }
-    __syncthreads();
-
-    const int nrow = row_tasks(D);
     constexpr int ncol = P / 2;
-    double esum = 0.0;
-    __shared__ T lam_s[2];
-    __shared__ int conv_s;
-    __shared__ RelaxAcc<T> racc[NW];
-    T relX = 0, relY = 0;
-    if (MODE == M_RELAX) {
-        relX = (T)rio[ridx].X[0];
-        relY = (T)rio[ridx].X[1];
-        if (tid == 0) { lam_s[0] = (T)rio[ridx].lam[0]; lam_s[1] = (T)rio[ridx].lam[1]; conv_s = 0; }
+
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
+    load_twiddles<P>(tw, twP, tid, NT);
+
+    const int s_begin = segs ? seg_off[blockIdx.x] : 0, s_end = segs ? seg_off[blockIdx.x + 1] : 1;
+    for (int sg = s_begin; sg < s_end; ++sg) {
+        int ridx, wait = 0, signal = 0;
+        long long sbeg = 0, nseg = nsteps;
+        if (segs) {
+            const Segment g = segs[sg];
+            ridx = g.rep; wait = g.wait; signal = g.signal; sbeg = g.step_begin; nseg = g.nsteps;
+        } else {
+            ridx = work[blockIdx.x];
+        }
+        if (tid == 0) {
+            ok_s = wait ? (int)wait_flag(flags + ridx) : 1;
+            if (!ok_s) atomicOr(status, ND_DEV_TIMEOUT);
+            r_sh = reps[ridx];
+        }
         __syncthreads();
-    }
-    const long long nst = (MODE == M_FIELD || MODE == M_ENERGY) ? 1 : (MODE == M_RELAX ? (long long)max_iter : nsteps);
-    long long n = 0;
-    T res_last = T(0);
-    for (n = 0; n < nst; ++n) {
-        for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
-            for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
-                const int q = qb + gw;
-                row_fwd_task<P, T>(q, q < nrow, D, msm, Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw, gid.gmask);
-            }
+        if (!ok_s) break;
+        const Replica &r = r_sh;
+        const int D = r.D, Dpad = r.Dpad, DD = D * D;
+        const long long cs = (long long)D * RS;           // spectrum component stride
+        const long long ms_s = (long long)D * Dpad;       // stage-state component stride
+        cplx<T> *spec = tw + R1 * G;
+        cplx<T> *scratch = spec + 3 * cs;
+        T *msm = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);
+        double *red = reinterpret_cast<double *>(msm + 3 * ms_s);
+        T *wsm = use_wbuf ? reinterpret_cast<T *>(red + 32) : nullptr;
+        cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
+
+        V3Ptr<T> yn{ybase + r.state_off, ms_s};
+        V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s};
+        V3Ptr<T> out{outbase ? outbase + r.state_off : nullptr, ms_s};
+        V3Ptr<T> ms{msm, ms_s};
+        V3Ptr<T> wb{wsm, ms_s};
+        for (int cell = tid; cell < DD; cell += NT) {
+            const int y = cell / D, x = cell - y * D;
+            const long long si = (long long)y * Dpad + x;
+            vec3<T> v = r.mask[cell] ? yn.ld(si) : vec3<T>{T(0), T(0), T(0)};
+            ms.st(si, v);
+        }
+        __syncthreads();
+
+        const int nrow = row_tasks(D);
+        double esum = 0.0;
+        T relX = 0, relY = 0;
+        if (MODE == M_RELAX) {
+            relX = (T)rio[ridx].X[0];
+            relY = (T)rio[ridx].X[1];
+            if (tid == 0) { lam_s[0] = (T)rio[ridx].lam[0]; lam_s[1] = (T)rio[ridx].lam[1]; conv_s = 0; }
             __syncthreads();
-            for (int qb = warp * GPW; qb < ncol; qb += NW * GPW) {
-                const int q = qb + gw;
-                col_task<P, T>(q, q < ncol, D, spec, cs, reinterpret_cast<const T *>(r.Ghat), gid.t, gid.lane, scr,
-                               tw, gid.gmask);
-            }
-            __syncthreads();
-            for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
-                const int q = qb + gw;
-                row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
-            }
-            __syncthreads();
-            const T *hr = reinterpret_cast<const T *>(spec);
-            const StepParams<T> sp = step_params<T>(r);
-            if (MODE == M_RELAX) {
-                // sweep: trial alignment with the current multipliers, reductions
-                const T eta = (T)eta_d, rc2 = (T)rc2_d, l0 = lam_s[0], l1 = lam_s[1];
-                RelaxAcc<T> a = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                for (int cell = tid; cell < DD; cell += NT) {
-                    if (!r.mask[cell]) continue;
-                    const int y = cell / D, x = cell - y * D;
-                    const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
-                    vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
-                    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
-                    relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, l0, l1, eta, a);
+        }
+        const long long nst = (MODE == M_FIELD || MODE == M_ENERGY) ? 1 : (MODE == M_RELAX ? (long long)max_iter : nseg);
+        long long n = 0;
+        T res_last = T(0);
+        for (n = 0; n < nst; ++n) {
+            for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
+                for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
+                    const int q = qb + gw;
+                    row_fwd_task<P, T>(q, q < nrow, D, msm, Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw, gid.gmask);
                 }
-                a.C0 = warp_sum_t(a.C0); a.C1 = warp_sum_t(a.C1); a.J00 = warp_sum_t(a.J00);
-                a.J01 = warp_sum_t(a.J01); a.J11 = warp_sum_t(a.J11); a.res = warp_max_t(a.res);
-                if ((tid & 31) == 0) racc[warp] = a;
                 __syncthreads();
-                if (tid == 0) {
-                    RelaxAcc<T> s = racc[0];
-                    for (int w = 1; w < NW; ++w) {
-                        s.C0 += racc[w].C0; s.C1 += racc[w].C1; s.J00 += racc[w].J00; s.J01 += racc[w].J01;
-                        s.J11 += racc[w].J11; s.res = max(s.res, racc[w].res);
+                for (int qb = warp * GPW; qb < ncol; qb += NW * GPW) {
+                    const int q = qb + gw;
+                    col_task<P, T>(q, q < ncol, D, spec, cs, reinterpret_cast<const T *>(r.Ghat), gid.t, gid.lane,
+                                   scr, tw, gid.gmask);
+                }
+                __syncthreads();
+                for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
+                    const int q = qb + gw;
+                    row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+                }
+                __syncthreads();
+                const T *hr = reinterpret_cast<const T *>(spec);
+                const StepParams<T> sp = step_params<T>(r);
+                if (MODE == M_RELAX) {
+                    // sweep: trial alignment with the current multipliers, reductions
+                    const T eta = (T)eta_d, rc2 = (T)rc2_d, l0 = lam_s[0], l1 = lam_s[1];
+                    RelaxAcc<T> a = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                    for (int cell = tid; cell < DD; cell += NT) {
+                        if (!r.mask[cell]) continue;
+                        const int y = cell / D, x = cell - y * D;
+                        const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
+                        vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                        const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+                        relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, l0, l1, eta, a);
                     }
-                    res_last = s.res;
-                    if (s.res < (T)tol_d) {
-                        conv_s = 1;
-                    } else {
-                        const T det = s.J00 * s.J11 - s.J01 * s.J01;
-                        if (det != T(0) && isfinite(det)) {
-                            lam_s[0] += -(s.J11 * s.C0 - s.J01 * s.C1) / det;
-                            lam_s[1] += -(-s.J01 * s.C0 + s.J00 * s.C1) / det;
+                    a.C0 = warp_sum_t(a.C0); a.C1 = warp_sum_t(a.C1); a.J00 = warp_sum_t(a.J00);
+                    a.J01 = warp_sum_t(a.J01); a.J11 = warp_sum_t(a.J11); a.res = warp_max_t(a.res);
+                    if ((tid & 31) == 0) racc[warp] = a;
+                    __syncthreads();
+                    if (tid == 0) {
+                        RelaxAcc<T> s = racc[0];
+                        for (int w = 1; w < NW; ++w) {
+                            s.C0 += racc[w].C0; s.C1 += racc[w].C1; s.J00 += racc[w].J00; s.J01 += racc[w].J01;
+                            s.J11 += racc[w].J11; s.res = max(s.res, racc[w].res);
+                        }
+                        res_last = s.res;
+                        if (s.res < (T)tol_d) {
+                            conv_s = 1;
+                        } else {
+                            const T det = s.J00 * s.J11 - s.J01 * s.J01;
+                            if (det != T(0) && isfinite(det)) {
+                                lam_s[0] += -(s.J11 * s.C0 - s.J01 * s.C1) / det;
+                                lam_s[1] += -(-s.J01 * s.C0 + s.J00 * s.C1) / det;
+                            }
                         }
                     }
+                    __syncthreads();
+                    if (conv_s) break;   // leaves the stage loop; the step loop stops below
+                    const T m0 = lam_s[0], m1 = lam_s[1];
+                    for (int cell = tid; cell < DD; cell += NT) {
+                        if (!r.mask[cell]) continue;
+                        const int y = cell / D, x = cell - y * D;
+                        const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
+                        vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                        const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+                        RelaxAcc<T> dummy = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                        ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, m0, m1, eta, dummy));
+                    }
+                    __syncthreads();
+                    continue;
                 }
-                __syncthreads();
-                if (conv_s) break;   // leaves the stage loop; the step loop stops below
-                const T m0 = lam_s[0], m1 = lam_s[1];
+                const unsigned long long step = step_base + r.step0 + (unsigned long long)(sbeg + n);
                 for (int cell = tid; cell < DD; cell += NT) {
                     if (!r.mask[cell]) continue;
                     const int y = cell / D, x = cell - y * D;
-                    const long long si = (long long)y * Dpad + x, hi = (long long)y * (2 * RS) + x;
+                    const long long si = (long long)y * Dpad + x;
+                    const long long hi = (long long)y * (2 * RS) + x;
                     vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
-                    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
-                    RelaxAcc<T> dummy = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                    ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, m0, m1, eta, dummy));
+                    if (MODE == M_ENERGY)
+                        esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step);
+                    else
+                        epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step, wb);
                 }
                 __syncthreads();
-                continue;
             }
+            if (MODE == M_RELAX && conv_s) break;
+        }
+        if (MODE == M_RELAX) {
+            // the relaxed state back to the caller's buffer
             for (int cell = tid; cell < DD; cell += NT) {
                 if (!r.mask[cell]) continue;
                 const int y = cell / D, x = cell - y * D;
                 const long long si = (long long)y * Dpad + x;
-                const long long hi = (long long)y * (2 * RS) + x;
-                vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
-                if (MODE == M_ENERGY)
-                    esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
-                else
-                    epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step_base + r.step0 + n);
+                yn.st(si, ms.ld(si));
             }
+            if (tid == 0) {
+                rio[ridx].lam[0] = (double)lam_s[0];
+                rio[ridx].lam[1] = (double)lam_s[1];
+                rio[ridx].resid = (double)res_last;
+                rio[ridx].iters = (int)n;
+                rio[ridx].status = conv_s ? 0 : 1;
+            }
+        }
+        if (MODE == M_ENERGY) {
+            esum = warp_sum(esum);
+            if ((tid & 31) == 0) red[warp] = esum;
             __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                for (int w = 0; w < NW; ++w) s += red[w];
+                red_out[ridx] = s;
+            }
         }
-        if (MODE == M_RELAX && conv_s) break;
-    }
-    if (MODE == M_RELAX) {
-        // the relaxed state back to the caller's buffer
-        for (int cell = tid; cell < DD; cell += NT) {
-            if (!r.mask[cell]) continue;
-            const int y = cell / D, x = cell - y * D;
-            const long long si = (long long)y * Dpad + x;
-            yn.st(si, ms.ld(si));
-        }
-        if (tid == 0) {
-            rio[ridx].lam[0] = (double)lam_s[0];
-            rio[ridx].lam[1] = (double)lam_s[1];
-            rio[ridx].resid = (double)res_last;
-            rio[ridx].iters = (int)n;
-            rio[ridx].status = conv_s ? 0 : 1;
-        }
-    }
-    if (MODE == M_ENERGY) {
-        esum = warp_sum(esum);
-        if ((tid & 31) == 0) red[warp] = esum;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NW; ++w) s += red[w];
-            red_out[ridx] = s;
+        __syncthreads();   // every write of this segment is done before the flag and the next segment
+        if (signal && tid == 0) {
+            __threadfence();
+            atomicExch(flags + ridx, 1);
         }
     }
 }
@@ -487,9 +545,44 @@ static cudaError_t launch_fused_t(const LaunchArgs &a)
     auto kern = k_fused<P, T, MODE, NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;
-    kern<<<a.nwork, NT, a.smem, a.stream>>>(a.reps, a.work, (T *)a.y, (T *)a.acc, (T *)a.out, a.red, (const cplx<T> *)a.tw,
-                                            a.nsteps, a.step_base, a.rio, a.eta, a.tol, a.rc2, a.max_iter);
-    return cudaGetLastError();
+    const Segment *segs = reinterpret_cast<const Segment *>(a.segs);
+    if (!segs) {
+        kern<<<a.nwork, NT, a.smem, a.stream>>>(a.reps, a.work, (T *)a.y, (T *)a.acc, (T *)a.out, a.red,
+                                                (const cplx<T> *)a.tw, a.nsteps, a.step_base, a.rio, a.eta, a.tol,
+                                                a.rc2, a.max_iter, nullptr, nullptr, nullptr, a.status, a.use_wbuf);
+        return cudaGetLastError();
+    }
+    // time-sliced schedule: the CTAs wait on one another, so they must all be
+    // resident at once -- a cooperative launch guarantees it or fails
+    const Replica *reps = a.reps;
+    const int *work = a.work;
+    T *y = (T *)a.y, *acc = (T *)a.acc, *out = (T *)a.out;
+    double *red = a.red;
+    const cplx<T> *tw = (const cplx<T> *)a.tw;
+    long long nsteps = a.nsteps;
+    unsigned long long step_base = a.step_base;
+    RelaxIO *rio = a.rio;
+    double eta = a.eta, tol = a.tol, rc2 = a.rc2;
+    int max_iter = a.max_iter, use_wbuf = a.use_wbuf;
+    const int *seg_off = a.seg_off;
+    int *flags = a.flags;
+    unsigned *status = a.status;
+    void *args[] = {(void *)&reps, (void *)&work, (void *)&y, (void *)&acc, (void *)&out, (void *)&red, (void *)&tw,
+                    (void *)&nsteps, (void *)&step_base, (void *)&rio, (void *)&eta, (void *)&tol, (void *)&rc2,
+                    (void *)&max_iter, (void *)&segs, (void *)&seg_off, (void *)&flags, (void *)&status,
+                    (void *)&use_wbuf};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(a.ncta), dim3(NT), args, a.smem, a.stream);
+}
+
+template <int P, typename T, int MODE>
+static int fused_occupancy(size_t smem)
+{
+    int n = 0;
+    cudaFuncSetAttribute(k_fused<P, T, MODE, FusedNT<P>::v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<P, T, MODE, FusedNT<P>::v>, FusedNT<P>::v, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
 }
 
 template <int P, typename T>

@@ -3,16 +3,39 @@
 
 namespace nd {
 
+static_assert(sizeof(Segment) == sizeof(SegmentHost), "segment layout");
+
 ND_DEFINE_TWIDDLE_UPLOAD(upload_tw_fused_f64)
 
-size_t fused_smem_f64(int P, int D, int Dpad)
+size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf)
 {
     switch (P) {
-    case 16: return fused_smem_bytes<16, double>(D, Dpad, FusedNT<16>::v);
-    case 32: return fused_smem_bytes<32, double>(D, Dpad, FusedNT<32>::v);
-    case 64: return fused_smem_bytes<64, double>(D, Dpad, FusedNT<64>::v);
-    case 128: return fused_smem_bytes<128, double>(D, Dpad, FusedNT<128>::v);
+    case 16: return fused_smem_bytes<16, double>(D, Dpad, FusedNT<16>::v, wbuf);
+    case 32: return fused_smem_bytes<32, double>(D, Dpad, FusedNT<32>::v, wbuf);
+    case 64: return fused_smem_bytes<64, double>(D, Dpad, FusedNT<64>::v, wbuf);
+    case 128: return fused_smem_bytes<128, double>(D, Dpad, FusedNT<128>::v, wbuf);
     default: return (size_t)-1;
+    }
+}
+
+template <int P>
+static int occ_p(int mode, size_t smem)
+{
+    switch (mode) {
+    case M_RK4: return fused_occupancy<P, double, M_RK4>(smem);
+    case M_HEUN: return fused_occupancy<P, double, M_HEUN>(smem);
+    default: return 0;
+    }
+}
+
+int fused_blocks_per_sm_f64(int P, int mode, size_t smem)
+{
+    switch (P) {
+    case 16: return occ_p<16>(mode, smem);
+    case 32: return occ_p<32>(mode, smem);
+    case 64: return occ_p<64>(mode, smem);
+    case 128: return occ_p<128>(mode, smem);
+    default: return 0;
     }
 }
 

@@ -34,10 +34,24 @@ struct LaunchArgs {
     RelaxIO *rio = nullptr;          // per replica, indexed like reps
     double eta = 0.5, tol = 1e-6, rc2 = 0.0;
     int max_iter = 0;
+    // time-sliced schedule (fused steppers): ncta CTAs run the segments
+    // segs[seg_off[b] .. seg_off[b+1]) and hand replicas over through flags
+    const void *segs = nullptr;
+    const int *seg_off = nullptr;
+    int *flags = nullptr;
+    int ncta = 0;
+    unsigned *status = nullptr;      // device status word (ND_DEV_* bits)
+    int use_wbuf = 0;                // keep the Heun predictor's normals in shared memory
+};
+
+struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh
+    int rep, wait, signal, pad;
+    long long step_begin, nsteps;
 };
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im);
-size_t fused_smem(int P, int prec, int D, int Dpad);
+size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf = false);
+int fused_blocks_per_sm(int P, int prec, int mode, size_t smem);
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
 cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD);
 size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] spectrum

@@ -1,0 +1,42 @@
+"""The time-sliced stepping schedule (more replicas than resident CTAs, so
+replicas change CTA between steps) gives bit-identical trajectories to the
+one-CTA-per-replica launch, for Heun and RK4."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1207_2192_gb300 as nd
+from paper_1207_2192_gb300 import Disk, Nanodisk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", ["heun", "rk4"])
+def test_time_sliced_schedule_is_bit_identical(mode):
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    disk = Disk(50e-9, 10e-9, alpha=0.01)
+    B = n_sm + 104 if n_sm >= 104 else 2 * n_sm       # above one CTA per SM for the P = 128 on-chip kernel
+    half = B // 2
+    X0 = np.stack([np.linspace(-6e-9, 6e-9, B), np.zeros(B)], 1)
+    big = Nanodisk([disk], [B], nd.ND_FP32)
+    m = big.empty_device()
+    big.init_vortex(m, X0)
+    parts = [Nanodisk([disk], [half], nd.ND_FP32), Nanodisk([disk], [B - half], nd.ND_FP32)]
+    T = np.full(B, 300.0)
+    seeds = np.arange(B, dtype=np.uint64) * 7 + 1
+    steps, dt = 7, 1e-14
+    ms = [p.empty_device() for p in parts]
+    parts[0].init_vortex(ms[0], X0[:half])
+    parts[1].init_vortex(ms[1], X0[half:])
+    if mode == "heun":
+        big.heun(m, steps, dt, T, seeds, step0=3)
+        parts[0].heun(ms[0], steps, dt, T[:half], seeds[:half], step0=3)
+        parts[1].heun(ms[1], steps, dt, T[half:], seeds[half:], step0=3)
+    else:
+        big.rk4(m, steps, dt)
+        parts[0].rk4(ms[0], steps, dt)
+        parts[1].rk4(ms[1], steps, dt)
+    assert nd.nd_check_status(big.h) == nd.ND_OK
+    n0 = ms[0].numel()
+    assert torch.equal(m[:n0], ms[0]) and torch.equal(m[n0:], ms[1])
+    assert not torch.equal(m[:n0], parts[0].to_device(parts[0].unpack(ms[0])) * 0)
