@@ -225,6 +225,28 @@ int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, uns
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Graph-captured stepping.  nd_graph_create records, once, the whole launch
+ * sequence of n_steps RK4 or Heun steps of every replica of the handle on
+ * the device state m (plus, if stats_sample, one nd_stats_sample) as a CUDA
+ * graph; the noise-step counter lives on the device and advances by n_steps
+ * at the end of every replay, so consecutive nd_graph_launch calls continue
+ * the Philox stream exactly as nd_step_heun with step0 advanced would (the
+ * trajectories are bit-identical).  The graph keeps its own copy of the
+ * per-replica parameters (dt, T, seeds, damping at creation time) and works
+ * on the buffer m given at creation.  Uneven multi-disk handles become one
+ * graph with a launch per FFT size class.  The paper has no counterpart
+ * (it is the batching of Sec. III's integrators).  nd_graph_nodes reports
+ * the number of kernel nodes of one replay. */
+#define ND_METHOD_RK4 0
+#define ND_METHOD_HEUN 1
+typedef struct nd_graph nd_graph;
+int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double dt_seconds, const double *T_kelvin,
+                    const unsigned long long *seed, unsigned long long step0, int stats_sample, nd_graph **out);
+int nd_graph_launch(nd_graph *g, void *stream);
+int nd_graph_nodes(const nd_graph *g, int *n_kernel_nodes);
+void nd_graph_destroy(nd_graph *g);
+
+/* ------------------------------------------------------------------------
  * Allocation-free Heun stepping.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code running
  * inside a framework that owns every device allocation through its own pool,

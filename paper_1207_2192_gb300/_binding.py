@@ -17,6 +17,7 @@ from . import build as _build
 
 ND_OK, ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NOT_CONVERGED, ND_ERR_NO_VORTEX, ND_ERR_TIMEOUT, ND_ERR_NAN = range(7)
 ND_FP32, ND_FP64 = 0, 1
+ND_METHOD_RK4, ND_METHOD_HEUN = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +62,10 @@ SIGNATURES = {
     "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
     "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
     "nd_check_status": (_I, [_P, _P]),
+    "nd_graph_create": (_I, [_P, _P, _I, _LL, _D, _P, _P, _ULL, _I, _P]),
+    "nd_graph_launch": (_I, [_P, _P]),
+    "nd_graph_nodes": (_I, [_P, _P]),
+    "nd_graph_destroy": (None, [_P]),
     "nd_stats_sample": (_I, [_P, _P, _D, _P]),
     "nd_stats_read": (_I, [_P, _P, _P, _P, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
@@ -257,3 +262,26 @@ def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
 def nd_check_status(h, stream=None):
     """Synchronise and return the device status code (ND_OK, ND_ERR_TIMEOUT, ND_ERR_NAN)."""
     return lib().nd_check_status(h, _stream(stream))
+
+
+def nd_graph_create(h, m, method, n_steps, dt_seconds, T_kelvin=None, seed=None, step0=0, stats_sample=False):
+    T = None if T_kelvin is None else np.ascontiguousarray(T_kelvin, dtype=np.float64)
+    s = None if seed is None else np.ascontiguousarray(seed, dtype=np.uint64)
+    g = ctypes.c_void_p()
+    _check(lib().nd_graph_create(h, _ptr(m), method, n_steps, dt_seconds, _ptr(T), _ptr(s), step0, int(stats_sample),
+                                 ctypes.byref(g)))
+    return g.value
+
+
+def nd_graph_launch(g, stream=None):
+    _check(lib().nd_graph_launch(g, _stream(stream)))
+
+
+def nd_graph_nodes(g):
+    n = ctypes.c_int()
+    _check(lib().nd_graph_nodes(g, ctypes.byref(n)))
+    return n.value
+
+
+def nd_graph_destroy(g):
+    lib().nd_graph_destroy(g)

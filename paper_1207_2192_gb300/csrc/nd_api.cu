@@ -122,6 +122,7 @@ struct nd_handle {
     int rbins = 0, vbins = 0;
     double r_max = 0, v_max = 0;
     double *core_d = nullptr;             // [B * 4] estimator output of the last sample
+    double *core_part = nullptr;          // [B][kCoreMaxBlocks][2] plaquette-scan candidates
     double *a_rep = nullptr;              // [B] cell edge per replica
     size_t max_smem = 0;
     int n_sm = 0;
@@ -220,13 +221,14 @@ static void build_segments(int Bc, long long n, int ncta, std::vector<SegmentHos
 
 // Run one mode over all replicas.  fp64 selects the FP64 kernels (with y a
 // double buffer of the state layout), otherwise the handle precision.
-static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st)
+static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st,
+                    const Replica *reps = nullptr)
 {
     const int prec = fp64 ? ND_PREC_FP64 : (h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32);
     for (auto &c : h->classes) {
         LaunchArgs a;
         a.mode = mode;
-        a.reps = h->reps_d;
+        a.reps = reps ? reps : h->reps_d;
         a.work = c.work_d;
         a.nwork = (int)c.reps.size();
         a.y = y;
@@ -236,6 +238,7 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         a.step_base = 0;
         a.stream = st;
         a.tw = (prec == ND_PREC_FP64) ? h->tw64[c.P] : h->tw32[c.P];
+        a.smem_optin = (int)h->max_smem;
         const bool fused = fp64 ? c.fused_fp64 : c.fused_main;
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
         if (fused) {
@@ -466,6 +469,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     if ((e = cudaMemset(h->status_d, 0, sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
     if ((e = cudaMallocHost(&h->rio_h, sizeof(RelaxIO) * B)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
     if ((e = cudaMalloc(&h->core_d, sizeof(double) * 4 * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->core_part, sizeof(double) * 2 * kCoreMaxBlocks * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->a_rep, sizeof(double) * B)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     {
         std::vector<double> av(B);
@@ -523,6 +527,7 @@ void nd_destroy(nd_handle *h)
     cudaFree(h->hist_r);
     cudaFree(h->hist_v);
     cudaFree(h->core_d);
+    cudaFree(h->core_part);
     cudaFree(h->a_rep);
     cudaFree(h->acc);
     cudaFree(h->ms);
@@ -807,7 +812,7 @@ int nd_vortex_core(nd_handle *h, const void *m, double *Xc_out, int *status, voi
                 return fail(ND_ERR_ARG, "vortex_core: disks of one size class must share lambda_ex / a");
         const double rcut = 4.0 * d.lambda / d.desc.a;
         ND_CUDA(launch_vortex_core(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d,
-                                   (int)c.reps.size(), md, rcut * rcut, h->aux_d, st));
+                                   (int)c.reps.size(), c.maxD, md, rcut * rcut, h->core_part, h->aux_d, st));
     }
     ND_CUDA(cudaMemcpyAsync(h->red_h, h->aux_d, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));
@@ -854,6 +859,19 @@ int nd_stats_reset(nd_handle *h, double r_max, int r_bins, double v_max, int v_b
     return ND_OK;
 }
 
+static int stats_launches(nd_handle *h, const void *m, double dt_sample_seconds, cudaStream_t st, const Replica *reps)
+{
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        const double rcut = 4.0 * d.lambda / d.desc.a;
+        ND_CUDA(launch_vortex_core(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, reps, c.work_d,
+                                   (int)c.reps.size(), c.maxD, m, rcut * rcut, h->core_part, h->core_d, st));
+        ND_CUDA(launch_stats_update(c.work_d, (int)c.reps.size(), h->core_d, h->a_rep, h->stats, h->hist_r, h->hist_v,
+                                    h->rbins, h->vbins, h->r_max, h->v_max, dt_sample_seconds, st));
+    }
+    return ND_OK;
+}
+
 int nd_stats_sample(nd_handle *h, const void *m, double dt_sample_seconds, void *stream)
 {
     if (int rc = check_handle(h)) return rc;
@@ -863,15 +881,7 @@ int nd_stats_sample(nd_handle *h, const void *m, double dt_sample_seconds, void 
     cudaStream_t st = (cudaStream_t)stream;
     fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
     upload_reps(h, st);
-    for (auto &c : h->classes) {
-        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
-        const double rcut = 4.0 * d.lambda / d.desc.a;
-        ND_CUDA(launch_vortex_core(h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32, h->reps_d, c.work_d,
-                                   (int)c.reps.size(), m, rcut * rcut, h->core_d, st));
-        ND_CUDA(launch_stats_update(c.work_d, (int)c.reps.size(), h->core_d, h->a_rep, h->stats, h->hist_r, h->hist_v,
-                                    h->rbins, h->vbins, h->r_max, h->v_max, dt_sample_seconds, st));
-    }
-    return ND_OK;
+    return stats_launches(h, m, dt_sample_seconds, st, h->reps_d);
 }
 
 int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, unsigned long long *v_hist, void *stream)
@@ -910,6 +920,107 @@ int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream)
     ND_CUDA(cudaMemcpyAsync(h->red_h, h->aux_d, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < 3 * B; ++i) out[i] = h->red_h[i];
+    return ND_OK;
+}
+
+struct nd_graph {
+    nd_handle *h = nullptr;
+    Replica *reps = nullptr;          // private parameter blocks (step counter advanced on the device)
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+void nd_graph_destroy(nd_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    cudaFree(g->reps);
+    delete g;
+}
+
+int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double dt_seconds, const double *T_kelvin,
+                    const unsigned long long *seed, unsigned long long step0, int stats_sample, nd_graph **out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(ND_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
+    if (n_steps < 1 || !(dt_seconds > 0)) return fail(ND_ERR_ARG, "n_steps >= 1 and dt > 0 required");
+    if (!m || !is_device_ptr(m)) return fail(ND_ERR_ARG, "a graph needs a device state buffer");
+    if (method == ND_METHOD_HEUN && (!T_kelvin || !seed)) return fail(ND_ERR_ARG, "T_kelvin and seed are required");
+    if (stats_sample && !h->stats) return fail(ND_ERR_ARG, "stats_sample needs nd_stats_reset first");
+    const int B = (int)h->rep_disk.size();
+    const int mode = method == ND_METHOD_RK4 ? M_RK4 : M_HEUN;
+    nd_graph *g = new nd_graph();
+    g->h = h;
+    auto bail = [&](int code, const std::string &msg) {
+        nd_graph_destroy(g);
+        return fail(code, msg);
+    };
+    cudaError_t e = cudaMalloc(&g->reps, sizeof(Replica) * B);
+    if (e != cudaSuccess) return bail(ND_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    fill_reps(h, h->prec == ND_FP64, dt_seconds, method == ND_METHOD_HEUN ? T_kelvin : nullptr,
+              method == ND_METHOD_HEUN ? seed : nullptr, step0);
+    e = cudaMemcpy(g->reps, h->reps_h, sizeof(Replica) * B, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(ND_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    // one plain run of the launch sequence prepares the cached schedules
+    // (allocations are not allowed inside a capture); it works on a scratch
+    // copy so the caller's state is untouched
+    {
+        void *tmp = nullptr;
+        if ((e = cudaMalloc(&tmp, h->elt * h->state_elems)) != cudaSuccess)
+            return bail(ND_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaMemcpy(tmp, m, h->elt * h->state_elems, cudaMemcpyDeviceToDevice);
+        Replica *r2 = nullptr;
+        cudaMalloc(&r2, sizeof(Replica) * B);
+        cudaMemcpy(r2, g->reps, sizeof(Replica) * B, cudaMemcpyDeviceToDevice);
+        int rc = run_mode(h, mode, false, tmp, nullptr, n_steps, 0, r2);
+        cudaDeviceSynchronize();
+        cudaFree(tmp);
+        cudaFree(r2);
+        if (rc) { std::string msg = g_err; return bail(rc, msg); }
+    }
+    if ((e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(ND_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    if ((e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail(ND_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    int rc = run_mode(h, mode, false, m, nullptr, n_steps, g->cap, g->reps);
+    if (rc == ND_OK && stats_sample) rc = stats_launches(h, m, n_steps * dt_seconds, g->cap, g->reps);
+    if (rc == ND_OK && launch_advance_steps(g->reps, B, n_steps, g->cap) != cudaSuccess) rc = ND_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap, &graph);
+    g->graph = graph;
+    if (rc) { std::string msg = g_err; return bail(rc, "capture: " + msg); }
+    if (e != cudaSuccess) return bail(ND_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+        return bail(ND_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    *out = g;
+    return ND_OK;
+}
+
+int nd_graph_launch(nd_graph *g, void *stream)
+{
+    if (!g || !g->exec) return fail(ND_ERR_ARG, "null graph");
+    ND_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return ND_OK;
+}
+
+int nd_graph_nodes(const nd_graph *g, int *n_kernel_nodes)
+{
+    if (!g || !g->graph || !n_kernel_nodes) return fail(ND_ERR_ARG, "null argument");
+    size_t n = 0;
+    ND_CUDA(cudaGraphGetNodes(g->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    ND_CUDA(cudaGraphGetNodes(g->graph, nodes.data(), &n));
+    int k = 0;
+    for (auto nd_ : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd_, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *n_kernel_nodes = k;
     return ND_OK;
 }
 

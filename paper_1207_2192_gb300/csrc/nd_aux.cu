@@ -199,30 +199,41 @@ cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, i
 
 // ------------------------------------------------------------ vortex core
 
-// Core position estimator (Section IV), one CTA per replica.  The plaquette
+// Core position estimator (Section IV) in two kernels.  The plaquette
 // windings and the m_z^2 corner sums are evaluated in double precision with
 // no fused multiply-adds, in the same order as the CPU reference, so both
 // take the same integer decisions from the same inputs.
+//   k_core_scan: grid (nblk, replicas), each CTA scans a strided share of the
+//     plaquettes for the winding +1 one with the largest corner sum (lowest
+//     index on ties) and writes its candidate;
+//   k_core_finish: one CTA per replica picks the best candidate (same rule)
+//     and forms the m_z^2-weighted centroid over the disk cells within
+//     4 lambda_ex of it, visiting only the bounding box of that circle.
+template <typename T> struct CoreAt {
+    const T *y;
+    long long cs;
+    int D, Dpad;
+    __device__ __forceinline__ double operator()(int cell, int c) const
+    {
+        const int j = cell / D, i = cell - j * D;
+        return (double)y[c * cs + (long long)j * Dpad + i];
+    }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_vortex_core(const Replica *reps, const int *work, const T *ybase, double rc2,
-                                                     double *out)
+__global__ void __launch_bounds__(256) k_core_scan(const Replica *reps, const int *work, const T *ybase, double *part,
+                                                   int nblk)
 {
     __shared__ double sw[256];
     __shared__ int si_[256];
-    __shared__ double sx[3][8];
-    const int ridx = work[blockIdx.x];
+    const int ridx = work[blockIdx.y];
     const Replica r = reps[ridx];
     const int D = r.D, tid = threadIdx.x;
-    const long long cs = (long long)D * r.Dpad;
-    const T *y = ybase + r.state_off;
-    auto at = [&](int cell, int c) -> double {
-        const int j = cell / D, i = cell - j * D;
-        return (double)y[c * cs + (long long)j * r.Dpad + i];
-    };
+    const CoreAt<T> at{ybase + r.state_off, (long long)D * r.Dpad, D, r.Dpad};
     double bw = -1.0;
     int bi = 0x7fffffff;
     const int np = (D - 1) * (D - 1);
-    for (int p = tid; p < np; p += 256) {
+    for (int p = blockIdx.x * 256 + tid; p < np; p += nblk * 256) {
         const int j = p / (D - 1), i = p - j * (D - 1);
         const int t = j * D + i;
         if (!(r.mask[t] && r.mask[t + 1] && r.mask[t + D] && r.mask[t + D + 1])) continue;
@@ -253,24 +264,53 @@ __global__ void __launch_bounds__(256) k_vortex_core(const Replica *reps, const 
         }
         __syncthreads();
     }
-    const int best = si_[0];
-    const bool found = sw[0] >= 0.0 && best != 0x7fffffff;
-    double cx = 0, cy = 0;
-    if (found) {
-        const int bj = best / D, bii = best - bj * D;
-        cx = bii + 0.5 - 0.5 * (D - 1);
-        cy = bj + 0.5 - 0.5 * (D - 1);
+    if (tid == 0) {
+        double *o = part + 2 * ((size_t)ridx * nblk + blockIdx.x);
+        o[0] = sw[0];
+        o[1] = (double)si_[0];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_core_finish(const Replica *reps, const int *work, const T *ybase,
+                                                     const double *part, int nblk, double rc2, double *out)
+{
+    __shared__ double sx[3][8];
+    __shared__ int best_s;
+    __shared__ double bw_s;
+    const int ridx = work[blockIdx.x];
+    const Replica r = reps[ridx];
+    const int D = r.D, tid = threadIdx.x;
+    const CoreAt<T> at{ybase + r.state_off, (long long)D * r.Dpad, D, r.Dpad};
+    if (tid == 0) {
+        double bw = -1.0;
+        int bi = 0x7fffffff;
+        for (int b = 0; b < nblk; ++b) {
+            const double w = part[2 * ((size_t)ridx * nblk + b)];
+            const int i = (int)part[2 * ((size_t)ridx * nblk + b) + 1];
+            if (w > bw || (w == bw && i < bi)) { bw = w; bi = i; }
+        }
+        best_s = bi;
+        bw_s = bw;
+    }
+    __syncthreads();
+    const int best = best_s;
+    const bool found = bw_s >= 0.0 && best != 0x7fffffff;
     double a0 = 0, a1 = 0, a2 = 0;
     if (found) {
-        for (int cell = tid; cell < D * D; cell += 256) {
+        const int bj = best / D, bii = best - bj * D;
+        const double cx = bii + 0.5 - 0.5 * (D - 1), cy = bj + 0.5 - 0.5 * (D - 1);
+        const int rc = (int)ceil(sqrt(rc2)) + 1;
+        const int i0 = max(0, bii - rc), i1 = min(D - 1, bii + 1 + rc), j0 = max(0, bj - rc), j1 = min(D - 1, bj + 1 + rc);
+        const int w = i1 - i0 + 1, nbox = w * (j1 - j0 + 1);
+        for (int k = tid; k < nbox; k += 256) {
+            const int j = j0 + k / w, i = i0 + k % w, cell = j * D + i;
             if (!r.mask[cell]) continue;
-            const int j = cell / D, i = cell - j * D;
             const double x = i - 0.5 * (D - 1), yy = j - 0.5 * (D - 1);
             const double dx = x - cx, dy = yy - cy;
             if (dx * dx + dy * dy >= rc2) continue;
-            const double z = at(cell, 2), w = z * z;
-            a0 += w; a1 += w * x; a2 += w * yy;
+            const double z = at(cell, 2), wz = z * z;
+            a0 += wz; a1 += wz * x; a2 += wz * yy;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -282,7 +322,7 @@ __global__ void __launch_bounds__(256) k_vortex_core(const Replica *reps, const 
     __syncthreads();
     if (tid == 0) {
         double s0 = 0, s1 = 0, s2 = 0;
-        for (int w = 0; w < 8; ++w) { s0 += sx[0][w]; s1 += sx[1][w]; s2 += sx[2][w]; }
+        for (int wv = 0; wv < 8; ++wv) { s0 += sx[0][wv]; s1 += sx[1][wv]; s2 += sx[2][wv]; }
         double *o = out + 4 * ridx;
         if (found && s0 > 0.0) { o[0] = s1 / s0; o[1] = s2 / s0; o[2] = 0.0; }
         else { o[0] = 0.0; o[1] = 0.0; o[2] = 1.0; }
@@ -290,11 +330,39 @@ __global__ void __launch_bounds__(256) k_vortex_core(const Replica *reps, const 
     }
 }
 
-cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, const void *y, double rc2,
-                               double *out, cudaStream_t st)
+int core_scan_blocks(int D)
 {
-    if (prec == ND_PREC_FP64) k_vortex_core<double><<<nwork, 256, 0, st>>>(reps, work, (const double *)y, rc2, out);
-    else k_vortex_core<float><<<nwork, 256, 0, st>>>(reps, work, (const float *)y, rc2, out);
+    const int np = (D - 1) * (D - 1);
+    int n = np / 4096;
+    return n < 1 ? 1 : (n > kCoreMaxBlocks ? kCoreMaxBlocks : n);
+}
+
+cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, int maxD, const void *y,
+                               double rc2, double *part, double *out, cudaStream_t st)
+{
+    const int nblk = core_scan_blocks(maxD);
+    dim3 g(nblk, nwork);
+    if (prec == ND_PREC_FP64) {
+        k_core_scan<double><<<g, 256, 0, st>>>(reps, work, (const double *)y, part, nblk);
+        k_core_finish<double><<<nwork, 256, 0, st>>>(reps, work, (const double *)y, part, nblk, rc2, out);
+    } else {
+        k_core_scan<float><<<g, 256, 0, st>>>(reps, work, (const float *)y, part, nblk);
+        k_core_finish<float><<<nwork, 256, 0, st>>>(reps, work, (const float *)y, part, nblk, rc2, out);
+    }
+    return cudaGetLastError();
+}
+
+// Advance the noise-step counter of every replica (graph replays continue the
+// Philox stream where the previous replay stopped).
+__global__ void k_advance_steps(Replica *reps, int n, long long steps)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) reps[r].step0 += (unsigned long long)steps;
+}
+
+cudaError_t launch_advance_steps(Replica *reps, int n, long long steps, cudaStream_t s)
+{
+    k_advance_steps<<<(n + 127) / 128, 128, 0, s>>>(reps, n, steps);
     return cudaGetLastError();
 }
 

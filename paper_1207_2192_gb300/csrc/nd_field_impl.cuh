@@ -538,6 +538,7 @@ constexpr size_t glob_smem_bytes()
     return sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G + (size_t)(NT / FFTGeom<P>::G) * FFTGeom<P>::SCRATCH);
 }
 
+
 template <int P, typename T, int MODE>
 static cudaError_t launch_fused_t(const LaunchArgs &a)
 {
@@ -571,7 +572,19 @@ static cudaError_t launch_fused_t(const LaunchArgs &a)
                     (void *)&nsteps, (void *)&step_base, (void *)&rio, (void *)&eta, (void *)&tol, (void *)&rc2,
                     (void *)&max_iter, (void *)&segs, (void *)&seg_off, (void *)&flags, (void *)&status,
                     (void *)&use_wbuf};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(a.ncta), dim3(NT), args, a.smem, a.stream);
+    // cudaLaunchKernelEx with the cooperative attribute is also legal inside a
+    // stream capture (graph kernel node)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ncta);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = a.smem;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void *)kern, args);
 }
 
 template <int P, typename T, int MODE>
@@ -635,6 +648,7 @@ static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
     cudaError_t e0 = cudaFuncSetAttribute(k_g_rows<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e0 == cudaSuccess) e0 = cudaFuncSetAttribute(k_g_cols<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e0 != cudaSuccess) return e0;
+
     dim3 gl((maxD * maxD + 255) / 256, a.nwork);
     k_g_load_stage<T><<<gl, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.y, (T *)a.ms);
     cudaError_t e = cudaGetLastError();

@@ -42,6 +42,7 @@ struct LaunchArgs {
     int ncta = 0;
     unsigned *status = nullptr;      // device status word (ND_DEV_* bits)
     int use_wbuf = 0;                // keep the Heun predictor's normals in shared memory
+    int smem_optin = 0;              // per-block shared-memory limit of the device
 };
 
 struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh
@@ -71,12 +72,15 @@ cudaError_t build_ghat_dl(int P, int D, double l, double dNx, double dNz, double
 cudaError_t launch_init_vortex(int prec, const Replica *reps, const int *work, int nwork, int maxD, void *y,
                                const double *X0_cells /*[nrep][2], units of a, device*/, const int *pol_chi,
                                double lambda_over_a, cudaStream_t st);
-cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, const void *y,
-                               double rc2, double *out /*[nrep][4]: xc, yc (units of a), status, pad*/,
+constexpr int kCoreMaxBlocks = 128;   // plaquette-scan CTAs per replica (candidates buffer: [B][128][2] doubles)
+int core_scan_blocks(int D);
+cudaError_t launch_vortex_core(int prec, const Replica *reps, const int *work, int nwork, int maxD, const void *y,
+                               double rc2, double *part, double *out /*[nrep][4]: xc, yc (units of a), status, cell*/,
                                cudaStream_t st);
 cudaError_t launch_stats_update(const int *work, int nwork, const double *core, const double *a_of_rep, StatsAcc *st,
                                 unsigned long long *hr, unsigned long long *hv, int rb, int vb, double r_max,
                                 double v_max, double dt, cudaStream_t s);
+cudaError_t launch_advance_steps(Replica *reps, int n, long long steps, cudaStream_t s);
 cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y,
                           double *out /*[nrep][3]*/, cudaStream_t st);
 cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st);

@@ -129,11 +129,11 @@ __device__ __forceinline__ void col_multiply_z(cplx<T> *vz, const T *Ghat, int k
     }
 }
 
-template <int P, typename T>
+template <int P, typename T, int RS = SpecGeom<P>::RS>
 __device__ __forceinline__ void col_load(cplx<T> *v, const cplx<T> *col, int D, int t, bool active)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    constexpr int G = Gm::G, R1 = Gm::R1;
 #pragma unroll
     for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
 #pragma unroll
@@ -143,11 +143,11 @@ __device__ __forceinline__ void col_load(cplx<T> *v, const cplx<T> *col, int D, 
     }
 }
 
-template <int P, typename T>
+template <int P, typename T, int RS = SpecGeom<P>::RS>
 __device__ __forceinline__ void col_store(const cplx<T> *v, cplx<T> *col, int D, int t, bool active)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    constexpr int G = Gm::G, R1 = Gm::R1;
     if (!active) return;
 #pragma unroll
     for (int o = 0; o < R1 / 2; ++o) {

@@ -1,0 +1,73 @@
+"""Parity at the full sizes of the benchmark configurations, in the launch
+configuration the benchmark times.
+
+* Large disk (R = 500 nm, P = 1024, global path) and R = 200 nm (P = 512):
+  the field on sampled cells against the oracle's direct sum at those cells.
+* Batched Heun, 256 replicas of R = 50 nm (time-sliced schedule over the
+  SMs): sampled replicas against the oracle's Heun trajectory.
+"""
+import numpy as np
+import pytest
+
+import ndsynth
+import paper_1207_2192_gb300 as nd
+from paper_1207_2192_gb300 import Disk, Nanodisk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("R,L", [(200e-9, 20e-9), (500e-9, 20e-9)])
+def test_large_disk_field_on_sampled_cells(O, R, L):
+    disk = Disk(R, L, hext=(0.0, 2e4, 0.0))
+    h = Nanodisk([disk], [2], nd.ND_FP32)
+    model = O.Model(R, L, hext=disk.hext)
+    grids = [ndsynth.random_unit_vectors(model.D, seed=21) * model.mask, model.init_vortex(12e-9, -4e-9)]
+    b = h.unpack(h.field(h.to_device(grids)))
+    inside = np.flatnonzero(model.mask.ravel())
+    cells = inside[ndsynth.sample_indices(len(inside), 24, seed=2)]
+    # include the rim, where the field is largest and least smooth
+    cells = np.concatenate([cells, inside[:4], inside[-4:]])
+    for r in range(2):
+        ref = model.field_at(grids[r], cells)
+        got = np.stack([b[r][:, c // model.D, c % model.D] for c in cells])
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-5 * scale
+
+
+def test_batched_heun_full_size_on_sampled_replicas(O):
+    disk = Disk(50e-9, 10e-9, alpha=0.01)
+    B = 256
+    h = Nanodisk([disk], [B], nd.ND_FP32)
+    model = O.Model(disk.R, disk.L, alpha=disk.alpha)
+    X0 = np.stack([np.linspace(-5e-9, 5e-9, B), np.zeros(B)], 1)
+    m = h.empty_device()
+    h.init_vortex(m, X0)
+    start = h.unpack(m)
+    T, seeds, dt, steps = np.full(B, 300.0), np.arange(B, dtype=np.uint64), 1e-14, 3
+    h.heun(m, steps, dt, T, seeds, step0=0)
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    out = h.unpack(m)
+    Ts = O.scaled_temperature(300.0, disk.A, disk.L)
+    for r in (0, 97, 151, 152, 255):
+        ref = model.heun(start[r], steps, model.dtau(dt), Ts, int(seeds[r]), 0)
+        assert np.max(np.abs(out[r] - ref)) < 1e-4
+        assert np.linalg.norm((out[r] - ref) * model.mask) <= 2e-4 * np.linalg.norm((ref - start[r]) * model.mask) + 1e-6
+
+
+def test_large_disk_heun_properties():
+    """P = 1024 Heun: unit norm kept, resumable bit for bit, noise matters."""
+    disk = Disk(500e-9, 20e-9, alpha=0.01)
+    h = Nanodisk([disk], [2], nd.ND_FP32)
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((2, 2)))
+    a, b = m.clone(), m.clone()
+    h.heun(a, 4, 1e-14, [300.0, 300.0], [1, 2], step0=0)
+    h.heun(b, 1, 1e-14, [300.0, 300.0], [1, 2], step0=0)
+    h.heun(b, 3, 1e-14, [300.0, 300.0], [1, 2], step0=1)
+    assert bool((a == b).all())
+    g = h.unpack(a)
+    mask = h.mask(0).astype(bool)
+    for r in range(2):
+        n = np.sqrt((g[r] ** 2).sum(0))[mask]
+        assert np.max(np.abs(n - 1)) < 1e-5
+    assert not np.allclose(g[0], g[1])
