@@ -31,8 +31,10 @@ def kF_map(h, xs, tol=1e-6, max_iter=40000, stream=None):
     E, dEdL = nd_energy(h.h, m, h.B, stream, with_dL=True)
     J = h.units[0][4]
     UJ = E * J
-    A = np.stack([np.ones_like(xs), 0.5 * xs ** 2], 1)
+    xn = xs / 1e-9                                   # fit in nanometres (well conditioned)
+    A = np.stack([np.ones_like(xn), 0.5 * xn ** 2], 1)
     coef, *_ = np.linalg.lstsq(A, UJ, rcond=None)
+    coef[1] /= 1e-18                                 # J/nm^2 -> J/m^2
     x1 = xs[1]
     kF_2pt = 2.0 * (UJ[1] - UJ[0]) / x1 ** 2
     dkF_dL = 2.0 * (dEdL[1] - dEdL[0]) / x1 ** 2
