@@ -192,6 +192,22 @@ class Workload:
         return 3
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (the slowest rank sets the time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Weak scaling: every rank runs its own replicas; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def l2_flush(torch, buf):
     buf.add_(1.0)   # writes 256 MB > 129 MB L2
 
@@ -242,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     # the stepping kernels alone (events around nd_step_heun on the same
     # stream, L2 flushed), for the roofline of the dominant kernel
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
@@ -254,12 +270,9 @@ def run_ours(args, rank, world, local_rank):
         wl.step += CHUNK
     torch.cuda.synchronize()
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    cu = wl.cell_updates_per_step() * args.steps * world
-    value = cu / (total_ms / 1e3)
+    cu_rank = wl.cell_updates_per_step() * args.steps
+    cu = cu_rank * world
+    value = whole_job_rate(cu_rank, world, total_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     host = torch.empty(wl.h.state_elems, dtype=torch.float32, pin_memory=True)
@@ -272,12 +285,8 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.steps):
         wl.nd.nd_step_heun(wl.h.h, host.data_ptr(), CHUNK, DT, wl.T, wl.seeds, wl.step, None)
         wl.step += CHUNK
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = cu / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = whole_job_rate(cu_rank, world, e2e_s)
 
     result = None
     if rank == 0:

@@ -66,6 +66,8 @@ extern "C" {
 #define ND_ERR_NAN 6            /* a non-finite value appeared in the state */
 
 #define ND_FP32 0               /* float state and fields, FP64 energies and core sums */
+#define ND_METHOD_RK4 0         /* stepping methods (nd_autotune, nd_graph_create) */
+#define ND_METHOD_HEUN 1
 #define ND_FP64 1               /* double everywhere */
 
 typedef struct nd_handle nd_handle;
@@ -225,6 +227,28 @@ int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, uns
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuning of the stepping schedule.  The replicas of a handle are grouped
+ * by padded FFT size P ("size classes"); each class can step on the fused
+ * on-chip kernel with one of up to three thread counts (which set how many
+ * FFT groups share the row and column passes) or on the global-memory path.
+ * nd_autotune times every candidate that fits, on a scratch copy of an
+ * analytic vortex state, for n_steps steps of the given method (and, for
+ * Heun, 300 K), and keeps the fastest per class for later nd_step_* calls and
+ * graphs.  nd_plan_info reports, for class cls (0-based, in order of first
+ * appearance), its P, replica count, the chosen plans (-1 default, 0..2 fused
+ * variant, 100 global path) and the fused kernel's threads per CTA (0: global
+ * path).  Returns ND_ERR_ARG for cls out of range.  The paper has no
+ * counterpart. */
+int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream);
+/* Force the plan of class cls for a method (-1 default, 0..2 fused variant,
+ * 100 global path); ND_ERR_ARG if it does not exist or does not fit.  Every
+ * plan computes the same arithmetic per element, so trajectories do not
+ * depend on it. */
+int nd_set_plan(nd_handle *h, int cls, int method, int plan);
+int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan_rk4, int *plan_heun, int *threads_rk4,
+                 int *threads_heun);
+
+/* ------------------------------------------------------------------------
  * Graph-captured stepping.  nd_graph_create records, once, the whole launch
  * sequence of n_steps RK4 or Heun steps of every replica of the handle on
  * the device state m (plus, if stats_sample, one nd_stats_sample) as a CUDA
@@ -237,8 +261,6 @@ int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
  * graph with a launch per FFT size class.  The paper has no counterpart
  * (it is the batching of Sec. III's integrators).  nd_graph_nodes reports
  * the number of kernel nodes of one replay. */
-#define ND_METHOD_RK4 0
-#define ND_METHOD_HEUN 1
 typedef struct nd_graph nd_graph;
 int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double dt_seconds, const double *T_kelvin,
                     const unsigned long long *seed, unsigned long long step0, int stats_sample, nd_graph **out);

@@ -63,6 +63,9 @@ SIGNATURES = {
     "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
     "nd_check_status": (_I, [_P, _P]),
     "nd_graph_create": (_I, [_P, _P, _I, _LL, _D, _P, _P, _ULL, _I, _P]),
+    "nd_autotune": (_I, [_P, _I, _D, _LL, _P]),
+    "nd_set_plan": (_I, [_P, _I, _I, _I]),
+    "nd_plan_info": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "nd_graph_launch": (_I, [_P, _P]),
     "nd_graph_nodes": (_I, [_P, _P]),
     "nd_graph_destroy": (None, [_P]),
@@ -285,3 +288,23 @@ def nd_graph_nodes(g):
 
 def nd_graph_destroy(g):
     lib().nd_graph_destroy(g)
+
+
+def nd_autotune(h, method, dt_seconds, n_steps=20, stream=None):
+    _check(lib().nd_autotune(h, method, dt_seconds, n_steps, _stream(stream)))
+
+
+def nd_plan_info(h, cls):
+    """dict(P, replicas, plan_rk4, plan_heun, threads_rk4, threads_heun) or None past the last class."""
+    v = [ctypes.c_int() for _ in range(6)]
+    rc = lib().nd_plan_info(h, cls, *[ctypes.byref(x) for x in v])
+    if rc != ND_OK:
+        return None
+    return dict(zip(["P", "replicas", "plan_rk4", "plan_heun", "threads_rk4", "threads_heun"], [x.value for x in v]))
+
+
+def nd_set_plan(h, cls, method, plan, check=True):
+    rc = lib().nd_set_plan(h, cls, method, plan)
+    if check:
+        _check(rc)
+    return rc

@@ -56,12 +56,15 @@ struct SizeClass {
     bool fused_fp64 = false;   // fused kernel in FP64 (energy)
     size_t smem_main = 0, smem_fp64 = 0;
     size_t smem_wbuf = 0;      // fused Heun with the normals kept in shared memory (0: does not fit)
+    int plan[2] = {-1, -1};    // stepping plan for RK4 / Heun: -1 default, 0..2 fused variant, kPlanGlobal
     // time-sliced schedule, cached per (mode, n_steps)
     SegmentHost *segs_d = nullptr;
     int *seg_off_d = nullptr;
     int seg_mode = -1, seg_ncta = 0;
     long long seg_nsteps = -1;
 };
+
+constexpr int kPlanGlobal = 100;
 
 int next_pow2_at_least(int n)
 {
@@ -222,10 +225,12 @@ static void build_segments(int Bc, long long n, int ncta, std::vector<SegmentHos
 // Run one mode over all replicas.  fp64 selects the FP64 kernels (with y a
 // double buffer of the state layout), otherwise the handle precision.
 static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st,
-                    const Replica *reps = nullptr)
+                    const Replica *reps = nullptr, int only_class = -1)
 {
     const int prec = fp64 ? ND_PREC_FP64 : (h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32);
-    for (auto &c : h->classes) {
+    for (int ci = 0; ci < (int)h->classes.size(); ++ci) {
+        if (only_class >= 0 && ci != only_class) continue;
+        auto &c = h->classes[ci];
         LaunchArgs a;
         a.mode = mode;
         a.reps = reps ? reps : h->reps_d;
@@ -239,18 +244,30 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         a.stream = st;
         a.tw = (prec == ND_PREC_FP64) ? h->tw64[c.P] : h->tw32[c.P];
         a.smem_optin = (int)h->max_smem;
-        const bool fused = fp64 ? c.fused_fp64 : c.fused_main;
+        bool fused = fp64 ? c.fused_fp64 : c.fused_main;
+        const bool stepping = (mode == M_HEUN || mode == M_RK4) && !fp64;
+        int variant = 0;
+        if (stepping) {
+            const int pl = c.plan[mode == M_RK4 ? 0 : 1];
+            if (pl == kPlanGlobal) fused = false;
+            else if (pl > 0) variant = pl;
+        }
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
         if (fused) {
             a.smem = fp64 ? c.smem_fp64 : c.smem_main;
             a.status = h->status_d;
-            if (mode == M_HEUN && !fp64 && c.smem_wbuf) {
-                a.smem = c.smem_wbuf;
-                a.use_wbuf = 1;
+            a.variant = variant;
+            if (variant != 0) a.smem = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, variant);
+            if (mode == M_HEUN && !fp64) {
+                const size_t w = variant == 0 ? c.smem_wbuf : fused_smem(c.P, prec, c.maxD, c.maxDpad, true, variant);
+                if (w && w != (size_t)-1 && w + 1024 <= h->max_smem) {
+                    a.smem = w;
+                    a.use_wbuf = 1;
+                }
             }
             if ((mode == M_HEUN || mode == M_RK4) && !fp64 && nsteps >= 2) {
                 // localise the replicas' indices to the class: segments refer to positions in c.reps
-                const int per_sm = fused_blocks_per_sm(c.P, prec, mode, a.smem);
+                const int per_sm = fused_blocks_per_sm(c.P, prec, mode, a.smem, variant);
                 const int ncta = per_sm * h->n_sm;
                 const int Bc = (int)c.reps.size();
                 if (per_sm > 0 && Bc > ncta) {
@@ -282,6 +299,7 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         } else {
             a.ms = fp64 ? (void *)h->ms64 : h->ms;
             a.spec = h->spec;
+            if (!a.ms || !a.spec) return fail(ND_ERR_ARG, "global-path buffers are not allocated");
             ND_CUDA(launch_global(c.P, prec, a, c.maxD));
         }
     }
@@ -920,6 +938,103 @@ int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream)
     ND_CUDA(cudaMemcpyAsync(h->red_h, h->aux_d, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < 3 * B; ++i) out[i] = h->red_h[i];
+    return ND_OK;
+}
+
+int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
+    if (n_steps < 1 || !(dt_seconds > 0)) return fail(ND_ERR_ARG, "n_steps >= 1 and dt > 0 required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int mode = method == ND_METHOD_RK4 ? M_RK4 : M_HEUN, slot = method == ND_METHOD_RK4 ? 0 : 1;
+    const int B = (int)h->rep_disk.size();
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    // candidates may include the global path: make sure its buffers exist
+    if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
+    if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
+    void *tmp = nullptr;
+    ND_CUDA(cudaMalloc(&tmp, h->elt * h->state_elems));
+    std::vector<double> X0(2 * B, 0.0);
+    int rc = nd_init_vortex(h, tmp, X0.data(), stream);
+    std::vector<double> T(B, 300.0);
+    std::vector<unsigned long long> sd(B);
+    for (int r = 0; r < B; ++r) sd[r] = (unsigned long long)r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ci = 0; ci < (int)h->classes.size() && rc == ND_OK; ++ci) {
+        SizeClass &c = h->classes[ci];
+        std::vector<int> cands;
+        for (int v = 0; v < 3; ++v) {
+            if (fused_variant_threads(c.P, v) == 0) continue;
+            const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, v);
+            if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(v);
+        }
+        cands.push_back(kPlanGlobal);
+        float best_ms = 1e30f;
+        int best = cands.front();
+        for (int cand : cands) {
+            c.plan[slot] = cand;
+            fill_reps(h, h->prec == ND_FP64, dt_seconds, mode == M_HEUN ? T.data() : nullptr, mode == M_HEUN ? sd.data() : nullptr, 0);
+            upload_reps(h, st);
+            rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, ci);   // warm-up, builds schedules
+            if (rc) break;
+            cudaEventRecord(e0, st);
+            rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, ci);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = cand; }
+        }
+        c.plan[slot] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tmp);
+    return rc;
+}
+
+int nd_set_plan(nd_handle *h, int cls, int method, int plan)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (cls < 0 || cls >= (int)h->classes.size()) return fail(ND_ERR_ARG, "no such size class");
+    if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
+    SizeClass &c = h->classes[cls];
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    if (plan == kPlanGlobal) {
+        if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
+        if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
+    } else if (plan >= 0) {
+        if (fused_variant_threads(c.P, plan) == 0) return fail(ND_ERR_ARG, "no such fused variant for this size");
+        const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, plan);
+        if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return fail(ND_ERR_ARG, "variant does not fit in shared memory");
+    } else if (plan != -1) {
+        return fail(ND_ERR_ARG, "plan must be -1, 0..2 or 100");
+    }
+    c.plan[method == ND_METHOD_RK4 ? 0 : 1] = plan;
+    return ND_OK;
+}
+
+int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan_rk4, int *plan_heun, int *threads_rk4,
+                 int *threads_heun)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (cls < 0 || cls >= (int)h->classes.size()) return fail(ND_ERR_ARG, "no such size class");
+    const SizeClass &c = h->classes[cls];
+    auto threads = [&](int pl) {
+        if (pl == kPlanGlobal) return 0;
+        if (!c.fused_main) return 0;
+        return fused_variant_threads(c.P, pl < 0 ? 0 : pl);
+    };
+    if (P) *P = c.P;
+    if (n_replicas) *n_replicas = (int)c.reps.size();
+    if (plan_rk4) *plan_rk4 = c.plan[0];
+    if (plan_heun) *plan_heun = c.plan[1];
+    if (threads_rk4) *threads_rk4 = threads(c.plan[0]);
+    if (threads_heun) *threads_heun = threads(c.plan[1]);
     return ND_OK;
 }
 

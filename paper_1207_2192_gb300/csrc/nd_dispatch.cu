@@ -7,10 +7,11 @@ cudaError_t upload_tw_fused_f32(const double *, const double *);
 cudaError_t upload_tw_fused_f64(const double *, const double *);
 cudaError_t upload_tw_glob_f32(const double *, const double *);
 cudaError_t upload_tw_glob_f64(const double *, const double *);
-size_t fused_smem_f32(int P, int D, int Dpad, bool wbuf);
-size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf);
-int fused_blocks_per_sm_f32(int P, int mode, size_t smem);
-int fused_blocks_per_sm_f64(int P, int mode, size_t smem);
+size_t fused_smem_f32(int P, int D, int Dpad, bool wbuf, int variant);
+size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf, int variant);
+int fused_blocks_per_sm_f32(int P, int mode, size_t smem, int variant);
+int fused_blocks_per_sm_f64(int P, int mode, size_t smem, int variant);
+int fused_variant_threads_f32(int P, int variant);
 cudaError_t launch_fused_f32(int P, const LaunchArgs &a);
 cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
 cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
@@ -25,15 +26,18 @@ cudaError_t upload_twiddle_constants(const double *re, const double *im)
     return upload_tw_glob_f64(re, im);
 }
 
-size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf)
+size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf, int variant)
 {
-    return prec == ND_PREC_FP64 ? fused_smem_f64(P, D, Dpad, wbuf) : fused_smem_f32(P, D, Dpad, wbuf);
+    return prec == ND_PREC_FP64 ? fused_smem_f64(P, D, Dpad, wbuf, variant) : fused_smem_f32(P, D, Dpad, wbuf, variant);
 }
 
-int fused_blocks_per_sm(int P, int prec, int mode, size_t smem)
+int fused_blocks_per_sm(int P, int prec, int mode, size_t smem, int variant)
 {
-    return prec == ND_PREC_FP64 ? fused_blocks_per_sm_f64(P, mode, smem) : fused_blocks_per_sm_f32(P, mode, smem);
+    return prec == ND_PREC_FP64 ? fused_blocks_per_sm_f64(P, mode, smem, variant)
+                                : fused_blocks_per_sm_f32(P, mode, smem, variant);
 }
+
+int fused_variant_threads(int P, int variant) { return fused_variant_threads_f32(P, variant); }
 
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a)
 {

@@ -220,8 +220,30 @@ __device__ __forceinline__ vec3<T> relax_cell(vec3<T> m, vec3<T> b, bool inW, T 
     return mp;
 }
 
+// Thread counts of the fused kernel per padded size: variant 0 is the default
+// (and the only one of the field, energy and relaxation modes); the stepping
+// modes also have the alternatives the autotuner (nd_autotune) times.
+template <int P, int V> struct NTV { static constexpr int v = 0; };
+template <> struct NTV<128, 0> { static constexpr int v = 512; };
+template <> struct NTV<128, 1> { static constexpr int v = 384; };
+template <> struct NTV<64, 0> { static constexpr int v = 384; };
+template <> struct NTV<64, 1> { static constexpr int v = 256; };
+template <> struct NTV<64, 2> { static constexpr int v = 512; };
+template <> struct NTV<32, 0> { static constexpr int v = 256; };
+template <> struct NTV<32, 1> { static constexpr int v = 128; };
+template <> struct NTV<16, 0> { static constexpr int v = 128; };
+template <> struct NTV<16, 1> { static constexpr int v = 64; };
+template <int P> struct FusedNT { static constexpr int v = NTV<P, 0>::v; };
+
+// Minimum resident CTAs the compiler must allow: the default thread count
+// keeps the whole register file for one CTA; the smaller variants are compiled
+// lean (up to 512 threads per SM resident) so that several CTAs can share an SM.
+template <int P, int NT> struct FusedMinBlocks {
+    static constexpr int v = (NT == NTV<P, 0>::v || NT >= 512) ? 1 : 512 / NT;
+};
+
 template <int P, typename T, int MODE, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
     k_fused(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
             T *__restrict__ accbase, T *__restrict__ outbase, double *__restrict__ red_out,
             const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base,
@@ -526,10 +548,17 @@ __global__ void k_g_load_stage(const Replica *__restrict__ reps, const int *__re
 
 // --------------------------------------------------------- launch helpers
 
-template <int P> struct FusedNT { static constexpr int v = 512; };
-template <> struct FusedNT<64> { static constexpr int v = 384; };
-template <> struct FusedNT<32> { static constexpr int v = 256; };
-template <> struct FusedNT<16> { static constexpr int v = 128; };
+
+inline int fused_nt(int P, int variant)
+{
+    switch (P) {
+    case 16: return variant == 0 ? NTV<16, 0>::v : variant == 1 ? NTV<16, 1>::v : 0;
+    case 32: return variant == 0 ? NTV<32, 0>::v : variant == 1 ? NTV<32, 1>::v : 0;
+    case 64: return variant == 0 ? NTV<64, 0>::v : variant == 1 ? NTV<64, 1>::v : variant == 2 ? NTV<64, 2>::v : 0;
+    case 128: return variant == 0 ? NTV<128, 0>::v : variant == 1 ? NTV<128, 1>::v : 0;
+    default: return 0;
+    }
+}
 template <int P> struct GlobNT { static constexpr int v = 256; };
 
 template <int P, typename T, int NT>
@@ -539,10 +568,9 @@ constexpr size_t glob_smem_bytes()
 }
 
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, int NT>
 static cudaError_t launch_fused_t(const LaunchArgs &a)
 {
-    constexpr int NT = FusedNT<P>::v;
     auto kern = k_fused<P, T, MODE, NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;
@@ -587,26 +615,53 @@ static cudaError_t launch_fused_t(const LaunchArgs &a)
     return cudaLaunchKernelExC(&cfg, (const void *)kern, args);
 }
 
-template <int P, typename T, int MODE>
-static int fused_occupancy(size_t smem)
+template <int P, typename T, int MODE, int NT>
+static int fused_occupancy_nt(size_t smem)
 {
     int n = 0;
-    cudaFuncSetAttribute(k_fused<P, T, MODE, FusedNT<P>::v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<P, T, MODE, FusedNT<P>::v>, FusedNT<P>::v, smem) !=
-        cudaSuccess)
-        return 0;
+    cudaFuncSetAttribute(k_fused<P, T, MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<P, T, MODE, NT>, NT, smem) != cudaSuccess) return 0;
     return n;
+}
+
+template <int P, typename T, int MODE>
+static int fused_occupancy(int variant, size_t smem)
+{
+    if (variant == 1) {
+        if constexpr (NTV<P, 1>::v > 0) return fused_occupancy_nt<P, T, MODE, NTV<P, 1>::v>(smem);
+        return 0;
+    }
+    if (variant == 2) {
+        if constexpr (NTV<P, 2>::v > 0) return fused_occupancy_nt<P, T, MODE, NTV<P, 2>::v>(smem);
+        return 0;
+    }
+    return fused_occupancy_nt<P, T, MODE, NTV<P, 0>::v>(smem);
+}
+
+template <int P, typename T, int MODE>
+static cudaError_t launch_stepper(const LaunchArgs &a)
+{
+    if (a.variant == 1) {
+        if constexpr (NTV<P, 1>::v > 0) return launch_fused_t<P, T, MODE, NTV<P, 1>::v>(a);
+        return cudaErrorInvalidValue;
+    }
+    if (a.variant == 2) {
+        if constexpr (NTV<P, 2>::v > 0) return launch_fused_t<P, T, MODE, NTV<P, 2>::v>(a);
+        return cudaErrorInvalidValue;
+    }
+    return launch_fused_t<P, T, MODE, NTV<P, 0>::v>(a);
 }
 
 template <int P, typename T>
 static cudaError_t launch_fused_p(const LaunchArgs &a)
 {
+    constexpr int NT0 = FusedNT<P>::v;
     switch (a.mode) {
-    case M_FIELD: return launch_fused_t<P, T, M_FIELD>(a);
-    case M_ENERGY: return launch_fused_t<P, T, M_ENERGY>(a);
-    case M_RK4: return launch_fused_t<P, T, M_RK4>(a);
-    case M_HEUN: return launch_fused_t<P, T, M_HEUN>(a);
-    case M_RELAX: return launch_fused_t<P, T, M_RELAX>(a);
+    case M_FIELD: return launch_fused_t<P, T, M_FIELD, NT0>(a);
+    case M_ENERGY: return launch_fused_t<P, T, M_ENERGY, NT0>(a);
+    case M_RK4: return launch_stepper<P, T, M_RK4>(a);
+    case M_HEUN: return launch_stepper<P, T, M_HEUN>(a);
+    case M_RELAX: return launch_fused_t<P, T, M_RELAX, NT0>(a);
     default: return cudaErrorInvalidValue;
     }
 }

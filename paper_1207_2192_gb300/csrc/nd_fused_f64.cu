@@ -7,37 +7,41 @@ static_assert(sizeof(Segment) == sizeof(SegmentHost), "segment layout");
 
 ND_DEFINE_TWIDDLE_UPLOAD(upload_tw_fused_f64)
 
-size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf)
+size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf, int variant)
 {
+    const int nt = fused_nt(P, variant);
+    if (nt == 0) return (size_t)-1;
     switch (P) {
-    case 16: return fused_smem_bytes<16, double>(D, Dpad, FusedNT<16>::v, wbuf);
-    case 32: return fused_smem_bytes<32, double>(D, Dpad, FusedNT<32>::v, wbuf);
-    case 64: return fused_smem_bytes<64, double>(D, Dpad, FusedNT<64>::v, wbuf);
-    case 128: return fused_smem_bytes<128, double>(D, Dpad, FusedNT<128>::v, wbuf);
+    case 16: return fused_smem_bytes<16, double>(D, Dpad, nt, wbuf);
+    case 32: return fused_smem_bytes<32, double>(D, Dpad, nt, wbuf);
+    case 64: return fused_smem_bytes<64, double>(D, Dpad, nt, wbuf);
+    case 128: return fused_smem_bytes<128, double>(D, Dpad, nt, wbuf);
     default: return (size_t)-1;
     }
 }
 
 template <int P>
-static int occ_p(int mode, size_t smem)
+static int occ_p(int mode, size_t smem, int variant)
 {
     switch (mode) {
-    case M_RK4: return fused_occupancy<P, double, M_RK4>(smem);
-    case M_HEUN: return fused_occupancy<P, double, M_HEUN>(smem);
+    case M_RK4: return fused_occupancy<P, double, M_RK4>(variant, smem);
+    case M_HEUN: return fused_occupancy<P, double, M_HEUN>(variant, smem);
     default: return 0;
     }
 }
 
-int fused_blocks_per_sm_f64(int P, int mode, size_t smem)
+int fused_blocks_per_sm_f64(int P, int mode, size_t smem, int variant)
 {
     switch (P) {
-    case 16: return occ_p<16>(mode, smem);
-    case 32: return occ_p<32>(mode, smem);
-    case 64: return occ_p<64>(mode, smem);
-    case 128: return occ_p<128>(mode, smem);
+    case 16: return occ_p<16>(mode, smem, variant);
+    case 32: return occ_p<32>(mode, smem, variant);
+    case 64: return occ_p<64>(mode, smem, variant);
+    case 128: return occ_p<128>(mode, smem, variant);
     default: return 0;
     }
 }
+
+int fused_variant_threads_f64(int P, int variant) { return fused_nt(P, variant); }
 
 cudaError_t launch_fused_f64(int P, const LaunchArgs &a)
 {

@@ -43,6 +43,7 @@ struct LaunchArgs {
     unsigned *status = nullptr;      // device status word (ND_DEV_* bits)
     int use_wbuf = 0;                // keep the Heun predictor's normals in shared memory
     int smem_optin = 0;              // per-block shared-memory limit of the device
+    int variant = 0;                 // fused-kernel thread-count variant (stepping modes)
 };
 
 struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh
@@ -51,8 +52,9 @@ struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh
 };
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im);
-size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf = false);
-int fused_blocks_per_sm(int P, int prec, int mode, size_t smem);
+size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf = false, int variant = 0);
+int fused_blocks_per_sm(int P, int prec, int mode, size_t smem, int variant = 0);
+int fused_variant_threads(int P, int variant);   // 0 if the variant does not exist
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
 cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD);
 size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] spectrum

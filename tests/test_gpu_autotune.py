@@ -1,0 +1,69 @@
+"""The stepping plans (fused-kernel thread-count variants, global path) give
+bit-identical trajectories, and the autotuner picks one of the valid plans
+per size class."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1207_2192_gb300 as nd
+from paper_1207_2192_gb300 import Disk, Nanodisk
+
+pytestmark = pytest.mark.gpu
+
+DISKS = [Disk(6e-9, 3e-9, alpha=0.02), Disk(13e-9, 3e-9, alpha=0.02), Disk(24e-9, 5e-9, alpha=0.02),
+         Disk(50e-9, 10e-9, alpha=0.02)]                    # P = 16, 32, 64, 128
+REPS = [3, 2, 2, 2]
+
+
+def classes(h):
+    out, i = [], 0
+    while True:
+        info = nd.nd_plan_info(h.h, i)
+        if info is None:
+            return out
+        out.append(info)
+        i += 1
+
+
+@pytest.mark.parametrize("method", [nd.ND_METHOD_HEUN, nd.ND_METHOD_RK4])
+def test_every_plan_gives_the_same_trajectory(method):
+    ref_h = Nanodisk(DISKS, REPS, nd.ND_FP32)
+    B = ref_h.B
+    X0 = np.zeros((B, 2))
+    T, seeds, dt = np.full(B, 300.0), np.arange(B, dtype=np.uint64), 1e-14
+
+    def run(h):
+        m = h.empty_device()
+        h.init_vortex(m, X0)
+        if method == nd.ND_METHOD_HEUN:
+            h.heun(m, 3, dt, T, seeds)
+        else:
+            h.rk4(m, 3, dt)
+        torch.cuda.synchronize()
+        return m
+
+    ref = run(ref_h)
+    cls = classes(ref_h)
+    assert [c["P"] for c in cls] == [16, 32, 64, 128]
+    tried = 0
+    for ci in range(len(cls)):
+        for plan in (0, 1, 2, 100):
+            h = Nanodisk(DISKS, REPS, nd.ND_FP32)
+            if nd.nd_set_plan(h.h, ci, method, plan, check=False) != nd.ND_OK:
+                continue
+            tried += 1
+            assert torch.equal(run(h), ref), (ci, plan)
+    assert tried >= 10
+
+
+def test_autotune_picks_valid_plans():
+    h = Nanodisk(DISKS, REPS, nd.ND_FP32)
+    nd.nd_autotune(h.h, nd.ND_METHOD_HEUN, 1e-14, 5)
+    for c in classes(h):
+        assert c["plan_heun"] in (0, 1, 2, 100)
+        assert c["plan_rk4"] == -1
+        assert (c["threads_heun"] > 0) == (c["plan_heun"] != 100)
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((h.B, 2)))
+    h.heun(m, 2, 1e-14, np.full(h.B, 300.0), np.arange(h.B, dtype=np.uint64))
+    assert nd.nd_check_status(h.h) == nd.ND_OK
