@@ -244,6 +244,7 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         a.stream = st;
         a.tw = (prec == ND_PREC_FP64) ? h->tw64[c.P] : h->tw32[c.P];
         a.smem_optin = (int)h->max_smem;
+        a.n_sm = h->n_sm;
         bool fused = fp64 ? c.fused_fp64 : c.fused_main;
         const bool stepping = (mode == M_HEUN || mode == M_RK4) && !fp64;
         int variant = 0;

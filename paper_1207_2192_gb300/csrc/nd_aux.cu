@@ -81,12 +81,10 @@ __global__ void k_ghat_pass1(int P, int D, const double *Gq, const double *cs, d
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int kx = i % KH, dy = (i / KH) % D, c = i / (KH * D);
         const double *g = Gq + (size_t)c * D * D + (size_t)dy * D;
-        double acc = 0.0;
-        for (int dx = 0; dx < D; ++dx) {
-            const int k = (int)(((long long)kx * dx) % P);
-            const double f = (c == 2) ? cs[2 * k + 1] : cs[2 * k];
-            acc += (dx == 0 ? 1.0 : 2.0) * g[dx] * f;
-        }
+        const double *fc = cs + (c == 2 ? 1 : 0);
+        double acc = g[0] * fc[0];
+        // phase index kx*dx mod P, advanced by kx per term (P is a power of two)
+        for (int dx = 1, k = kx; dx < D; ++dx, k = (k + kx) & (P - 1)) acc += 2.0 * g[dx] * fc[2 * k];
         T1[i] = acc;
     }
 }
@@ -105,12 +103,9 @@ __global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const 
         double v[4];
         for (int c = 0; c < 4; ++c) {
             const double *t1 = T1 + (size_t)c * D * KH + kx;
-            double acc = 0.0;
-            for (int dy = 0; dy < D; ++dy) {
-                const int k = (int)(((long long)ky * dy) % P);
-                const double f = (c == 2) ? cs[2 * k + 1] : cs[2 * k];
-                acc += (dy == 0 ? 1.0 : 2.0) * t1[(size_t)dy * KH] * f;
-            }
+            const double *fc = cs + (c == 2 ? 1 : 0);
+            double acc = t1[0] * fc[0];
+            for (int dy = 1, k = ky; dy < D; ++dy, k = (k + ky) & (P - 1)) acc += 2.0 * t1[(size_t)dy * KH] * fc[2 * k];
             v[c] = (c == 2) ? -acc : acc;
         }
         const double kex = with_exchange ? 2.0 * cs[2 * kx] + 2.0 * cs[2 * ky] : 0.0;

@@ -197,25 +197,4 @@ __device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const
     for (int o = 0; o < R2 * K2; ++o) v[o] = o_[o];
 }
 
-// Mirror values: for each register o (element k = t + G*o) return the value
-// the group holds at element (P - k) mod P.  Those live on lane (G - t) mod G,
-// register (R1 - 1 - o) for t > 0 and (R1 - o) mod R1 for t = 0.
-// The shuffle names only the group's own lanes (gmask): groups of one warp
-// may be on different branches (e.g. the packed real columns).
-template <int P, typename T>
-__device__ __forceinline__ void mirror_group(const cplx<T> *v, cplx<T> *w, int t, int lane, unsigned gmask)
-{
-    using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1;
-    int src = (lane - t) + ((G - t) & (G - 1));
-    cplx<T> r[R1];
-#pragma unroll
-    for (int q = 0; q < R1; ++q) {
-        r[q].x = __shfl_sync(gmask, v[q].x, src);
-        r[q].y = __shfl_sync(gmask, v[q].y, src);
-    }
-#pragma unroll
-    for (int o = 0; o < R1; ++o) w[o] = (t == 0) ? r[(R1 - o) % R1] : r[R1 - 1 - o];
-}
-
 }  // namespace nd

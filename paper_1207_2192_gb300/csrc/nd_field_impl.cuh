@@ -491,6 +491,86 @@ __global__ void __launch_bounds__(NT)
                    scratch + gid.group * Gm::SCRATCH, tw, gid.gmask);
 }
 
+// Column pass for the large grids, one FFT group per (column, component):
+// groups 3j, 3j+1, 3j+2 of a CTA take components x, y, z of one column task,
+// so a thread holds a single column (R1 points) instead of the x and y
+// columns together, and the register budget leaves room for five CTAs per
+// SM.  The in-plane tensor couples x and y: after the forward transforms the
+// x and y groups leave their spectra in their own scratch areas, the CTA
+// syncs, and each group reads its partner's.  The packed real columns
+// (task 0) need no exchange (G_xy vanishes there).  The grid is persistent:
+// each CTA fills its twiddle table once and walks the (replica, column block)
+// tasks with a grid stride.
+template <int P, typename T> struct ColSplit {
+    static constexpr int NT = 96;                          // three groups of G = 32, six of 16, twelve of 8
+    static constexpr int CPB = NT / FFTGeom<P>::G / 3;     // column tasks per CTA
+    static constexpr int NCB = (P / 2 + CPB - 1) / CPB;
+    // resident CTAs per SM the kernel is compiled for (FP64 columns take twice the registers)
+    static constexpr int MINB = sizeof(T) == 8 ? 2 : 5;
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(ColSplit<P, T>::NT, ColSplit<P, T>::MINB)
+    k_g_cols_split(const Replica *__restrict__ reps, const int *__restrict__ work, int nwork,
+                   cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP)
+{
+    using Gm = FFTGeom<P>;
+    using CS = ColSplit<P, T>;
+    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH, NT = CS::NT, CPB = CS::CPB;
+    static_assert(NT % (3 * G) == 0, "three groups per column");
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
+    cplx<T> *scratch = tw + R1 * G;
+    const int tid = threadIdx.x;
+    load_twiddles<P>(tw, twP, tid, NT);
+    __syncthreads();
+    GroupId<P> gid(tid);
+    const int j = gid.group / 3, c = gid.group - 3 * j, t = gid.t;
+    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
+    const cplx<T> *other = scratch + (gid.group + (c == 0 ? 1 : -1)) * Gm::SCRATCH;   // used by c < 2 only
+    for (int task = blockIdx.x; task < nwork * CS::NCB; task += gridDim.x) {
+        const int wi = task / CS::NCB, q = (task - wi * CS::NCB) * CPB + j;
+        const Replica &r = reps[work[wi]];
+        const int D = r.D;
+        const bool active = q < P / 2, packed = (q == 0);
+        const int kx = (active && q > 0) ? q : 1;   // idle groups still transform; keep their table reads in range
+        cplx<T> *col = specbase + r.spec_off + c * (long long)D * SpecGeom<P>::RS;
+        const T *Ghat = reinterpret_cast<const T *>(r.Ghat);
+        cplx<T> v[R1];
+        if (packed) {
+            packed_col_fwd<P, T>(v, c, active, D, col, Ghat, t, gid.lane, scr, tw, gid.gmask);
+        } else {
+            col_load<P>(v, col + kx, D, t, active);
+            fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gid.gmask);
+            if (c < 2) {
+#pragma unroll
+                for (int o = 0; o < R1; ++o) scr[o * G + t] = v[o];
+            }
+        }
+        __syncthreads();
+        if (!packed) {
+            if (c < 2) {
+#pragma unroll
+                for (int o = 0; o < R1; ++o) {
+                    const int ky = t + G * o;
+                    const bool up = ky <= P / 2;
+                    const int kyr = up ? ky : P - ky;
+                    GhatVal<T> g = load_ghat<T>(Ghat, kx * KH + kyr);
+                    const T gxy = up ? g.xy : -g.xy;     // G_xy is odd in ky
+                    const cplx<T> w = other[o * G + t];
+                    v[o] = c == 0 ? tensor_row(g.xx, v[o], gxy, w) : tensor_row(gxy, w, g.yy, v[o]);
+                }
+            } else {
+                col_multiply_z<P>(v, Ghat, kx, t);
+            }
+        }
+        __syncthreads();   // the partner's spectrum is read before the scratch is reused
+        fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gid.gmask);
+        if (packed) packed_col_store<P, T>(v, active, D, col, t);
+        else col_store<P>(v, col + kx, D, t, active);
+    }
+}
+
 // Elementwise epilogue of the global path.  grid = (cell blocks, replicas).
 template <int P, typename T, int MODE>
 __global__ void __launch_bounds__(256)
@@ -560,6 +640,8 @@ inline int fused_nt(int P, int variant)
     }
 }
 template <int P> struct GlobNT { static constexpr int v = 256; };
+// The split column pass runs from P = 256 up.
+template <int P> struct GlobSplit { static constexpr bool v = P >= 256; };
 
 template <int P, typename T, int NT>
 constexpr size_t glob_smem_bytes()
@@ -682,7 +764,15 @@ static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode,
     dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork), gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
     const size_t sm = glob_smem_bytes<P, T, NT>();
     k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 0);
-    k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+    if constexpr (GlobSplit<P>::v) {
+        using CS = ColSplit<P, T>;
+        const int ntask = a.nwork * CS::NCB;
+        const int grid = ntask < a.n_sm * CS::MINB ? ntask : a.n_sm * CS::MINB;
+        k_g_cols_split<P, T><<<grid, CS::NT, glob_smem_bytes<P, T, CS::NT>(), a.stream>>>(
+            a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+    } else {
+        k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+    }
     k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 1);
     dim3 ge((maxD * maxD + 255) / 256, a.nwork);
     switch (mode) {
@@ -702,6 +792,11 @@ static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
     const int sm = (int)glob_smem_bytes<P, T, NT>();
     cudaError_t e0 = cudaFuncSetAttribute(k_g_rows<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e0 == cudaSuccess) e0 = cudaFuncSetAttribute(k_g_cols<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if constexpr (GlobSplit<P>::v) {
+        if (e0 == cudaSuccess)
+            e0 = cudaFuncSetAttribute(k_g_cols_split<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)glob_smem_bytes<P, T, ColSplit<P, T>::NT>());
+    }
     if (e0 != cudaSuccess) return e0;
 
     dim3 gl((maxD * maxD + 255) / 256, a.nwork);

@@ -44,6 +44,7 @@ struct LaunchArgs {
     int use_wbuf = 0;                // keep the Heun predictor's normals in shared memory
     int smem_optin = 0;              // per-block shared-memory limit of the device
     int variant = 0;                 // fused-kernel thread-count variant (stepping modes)
+    int n_sm = 1;                    // multiprocessors of the device (persistent grids)
 };
 
 struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh

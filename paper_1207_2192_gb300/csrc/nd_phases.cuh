@@ -5,8 +5,7 @@
 //
 // Spectrum layout: spec[c][y][RS] complex, c = x, y, z; row y = 0..D-1 of the
 // zero-padded P x P grid (rows D..P-1 are zero and never stored); column
-// kx = 0..P/2 of the half spectrum; RS = P/2 + 2 words per row so that the
-// column pass reads conflict-free.  After the inverse row pass the same rows,
+// kx = 0..P/2 of the half spectrum; RS words per row (SpecGeom).  After the inverse row pass the same rows,
 // viewed as real arrays, hold the field b' = exchange + (a^2/lambda^2) h^M.
 //
 // Row pass (forward): the two real rows m_x(y), m_y(y) are transformed as one
@@ -23,7 +22,10 @@
 namespace nd {
 
 template <int P> struct SpecGeom {
-    static constexpr int RS = (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);
+    // on chip (P <= 128) the two padding words keep the column reads free of
+    // bank conflicts; in global memory (P >= 256) four start each row on a
+    // 32-byte sector, so the row passes move whole sectors
+    static constexpr int RS = (P >= 256) ? (P / 2 + 4) : (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);
     static constexpr int KH = P / 2 + 1;   // kernel table side
 };
 
@@ -40,6 +42,23 @@ template <> __device__ __forceinline__ GhatVal<double> load_ghat<double>(const d
     double2 a = __ldg(reinterpret_cast<const double2 *>(G) + 2 * idx);
     double2 b = __ldg(reinterpret_cast<const double2 *>(G) + 2 * idx + 1);
     return {a.x, a.y, b.x, b.y};
+}
+
+// Mirror element through the group's scratch: mirror_put stores the group's
+// transform in natural order (element k at scr[k]); after a __syncwarp,
+// mirror_get(scr, k) returns element (P - k) mod P.  The caller syncs the
+// group again before the scratch is reused.
+template <int P, typename T>
+__device__ __forceinline__ void mirror_put(const cplx<T> *v, cplx<T> *scr, int t)
+{
+    using Gm = FFTGeom<P>;
+#pragma unroll
+    for (int o = 0; o < Gm::R1; ++o) scr[t + Gm::G * o] = v[o];
+}
+template <int P, typename T>
+__device__ __forceinline__ cplx<T> mirror_get(const cplx<T> *scr, int k)
+{
+    return scr[(P - k) & (P - 1)];
 }
 
 // Number of row tasks: D complex xy rows plus ceil(D/2) z row pairs.
@@ -76,26 +95,38 @@ __device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T 
         }
     }
     fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
-    cplx<T> w[R1];
-    mirror_group<P>(v, w, t, lane, gmask);
-    if (!active) return;
+    mirror_put<P>(v, scr, t);
+    __syncwarp(gmask);
     cplx<T> *dA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
     cplx<T> *dB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
     const bool hasB = isxy || (y1 < D);
+    if (active) {
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
-        const int k = t + G * o;
-        if (k <= P / 2) {
-            const T h = T(0.5);
-            cplx<T> A = {h * (v[o].x + w[o].x), h * (v[o].y - w[o].y)};
-            cplx<T> B = {h * (v[o].y + w[o].y), -h * (v[o].x - w[o].x)};
-            dA[k] = A;
-            if (hasB) dB[k] = B;
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            if (k <= P / 2) {
+                const cplx<T> w = mirror_get<P>(scr, k);
+                const T h = T(0.5);
+                cplx<T> A = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
+                cplx<T> B = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
+                dA[k] = A;
+                if (hasB) dB[k] = B;
+            }
         }
     }
+    __syncwarp(gmask);
 }
 
 // --------------------------------------------------------------- columns
+
+// One row of the in-plane 2x2 block applied to the pair (a, b) = (X, Y):
+// g0 a + g1 b.  Every path computes the block through this helper, so all
+// schedules round the product identically.
+template <typename T>
+__device__ __forceinline__ cplx<T> tensor_row(T g0, cplx<T> a, T g1, cplx<T> b)
+{
+    return {g0 * a.x + g1 * b.x, g0 * a.y + g1 * b.y};
+}
 
 template <int P, typename T>
 __device__ __forceinline__ void col_multiply(cplx<T> *vx, cplx<T> *vy, const T *Ghat, int kx, int t)
@@ -110,8 +141,8 @@ __device__ __forceinline__ void col_multiply(cplx<T> *vx, cplx<T> *vy, const T *
         GhatVal<T> g = load_ghat<T>(Ghat, kx * KH + kyr);
         const T gxy = up ? g.xy : -g.xy;     // G_xy is odd in ky
         cplx<T> a = vx[o], b = vy[o];
-        vx[o] = {g.xx * a.x + gxy * b.x, g.xx * a.y + gxy * b.y};
-        vy[o] = {gxy * a.x + g.yy * b.x, gxy * a.y + g.yy * b.y};
+        vx[o] = tensor_row(g.xx, a, gxy, b);
+        vy[o] = tensor_row(gxy, a, g.yy, b);
     }
 }
 
@@ -156,6 +187,62 @@ __device__ __forceinline__ void col_store(const cplx<T> *v, cplx<T> *col, int D,
     }
 }
 
+// Packed pair of real columns kx = 0 and kx = P/2 of component c (spectrum
+// column base col): load as c0 + i c_{P/2}, forward transform, separate the
+// two spectra with the mirror element, scale each by its diagonal kernel entry
+// and re-pack, ready for the inverse transform.
+template <int P, typename T>
+__device__ __forceinline__ void packed_col_fwd(cplx<T> *v, int c, bool active, int D, const cplx<T> *col,
+                                               const T *Ghat, int t, int lane, cplx<T> *scr, const cplx<T> *tw,
+                                               unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH;
+#pragma unroll
+    for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+    for (int o = 0; o < R1 / 2; ++o) {
+        const int y = t + G * o;
+        if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
+    }
+    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
+    mirror_put<P>(v, scr, t);
+    __syncwarp(gmask);
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int ky = t + G * o;
+        const int kyr = ky <= P / 2 ? ky : P - ky;
+        const cplx<T> w = mirror_get<P>(scr, ky);
+        const int comp = c == 2 ? 3 : c;    // the diagonal entry: xx, yy or zz
+        const T s0 = __ldg(Ghat + 4 * kyr + comp);
+        const T s1 = __ldg(Ghat + 4 * ((P / 2) * KH + kyr) + comp);
+        const T h = T(0.5);
+        cplx<T> F0 = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
+        cplx<T> F1 = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
+        F0 = cscale(F0, s0);
+        F1 = cscale(F1, s1);
+        v[o] = {F0.x - F1.y, F0.y + F1.x};
+    }
+    __syncwarp(gmask);
+}
+
+// Rows < D of the inverse-transformed packed pair back to the two real columns.
+template <int P, typename T>
+__device__ __forceinline__ void packed_col_store(const cplx<T> *v, bool active, int D, cplx<T> *col, int t)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    if (!active) return;
+#pragma unroll
+    for (int o = 0; o < R1 / 2; ++o) {
+        const int y = t + G * o;
+        if (y < D) {
+            col[(long long)y * RS] = {v[o].x, T(0)};
+            col[(long long)y * RS + P / 2] = {v[o].y, T(0)};
+        }
+    }
+}
+
 // Column task q = 0..P/2-1: q = 0 is the packed pair of real columns kx = 0
 // and kx = P/2, q >= 1 is column kx = q.
 template <int P, typename T>
@@ -188,44 +275,10 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
     // packed real columns: z = c0 + i c_{P/2}; G_xy vanishes on both columns
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-        cplx<T> *col = spec + c * cstride;
         cplx<T> v[R1];
-#pragma unroll
-        for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
-#pragma unroll
-        for (int o = 0; o < R1 / 2; ++o) {
-            const int y = t + G * o;
-            if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
-        }
-        fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
-        cplx<T> w[R1];
-        mirror_group<P>(v, w, t, lane, gmask);
-#pragma unroll
-        for (int o = 0; o < R1; ++o) {
-            const int ky = t + G * o;
-            const int kyr = ky <= P / 2 ? ky : P - ky;
-            GhatVal<T> g0 = load_ghat<T>(Ghat, kyr);
-            GhatVal<T> g1 = load_ghat<T>(Ghat, (P / 2) * KH + kyr);
-            const T s0 = c == 0 ? g0.xx : (c == 1 ? g0.yy : g0.zz);
-            const T s1 = c == 0 ? g1.xx : (c == 1 ? g1.yy : g1.zz);
-            const T h = T(0.5);
-            cplx<T> F0 = {h * (v[o].x + w[o].x), h * (v[o].y - w[o].y)};
-            cplx<T> F1 = {h * (v[o].y + w[o].y), -h * (v[o].x - w[o].x)};
-            F0 = cscale(F0, s0);
-            F1 = cscale(F1, s1);
-            v[o] = {F0.x - F1.y, F0.y + F1.x};
-        }
+        packed_col_fwd<P, T>(v, c, active, D, spec + c * cstride, Ghat, t, lane, scr, tw, gmask);
         fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
-        if (active) {
-#pragma unroll
-            for (int o = 0; o < R1 / 2; ++o) {
-                const int y = t + G * o;
-                if (y < D) {
-                    col[(long long)y * RS] = {v[o].x, T(0)};
-                    col[(long long)y * RS + P / 2] = {v[o].y, T(0)};
-                }
-            }
-        }
+        packed_col_store<P, T>(v, active, D, spec + c * cstride, t);
     }
 }
 
