@@ -233,15 +233,35 @@ __global__ void __launch_bounds__(256) k_core_scan(const Replica *reps, const in
         const int t = j * D + i;
         if (!(r.mask[t] && r.mask[t + 1] && r.mask[t + D] && r.mask[t + D + 1])) continue;
         const int c[4] = {t, t + 1, t + D + 1, t + D};
-        double s = 0.0;
+        // The winding is decided in double precision.  A single-precision pass
+        // settles every plaquette whose angle sum lies within a quarter turn
+        // of a multiple of 2 pi (its error, ~1e-6 rad, is far below that
+        // margin, so the double sum rounds to the same integer); only the
+        // others, and plaquettes with an in-plane component too small for
+        // single-precision products, are summed again in double.
+        float sf = 0.0f, amin = 1.0f;
         for (int q = 0; q < 4; ++q) {
             const int p0 = c[q], p1 = c[(q + 1) & 3];
-            const double ax = at(p0, 0), ay = at(p0, 1), bx = at(p1, 0), by = at(p1, 1);
-            const double cr = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
-            const double dt = __dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by));
-            s = __dadd_rn(s, atan2(cr, dt));
+            const float ax = (float)at(p0, 0), ay = (float)at(p0, 1), bx = (float)at(p1, 0), by = (float)at(p1, 1);
+            sf += atan2f(ax * by - ay * bx, ax * bx + ay * by);
+            amin = fminf(amin, ax * ax + ay * ay);
         }
-        if (llround(s / (2.0 * M_PI)) != 1) continue;
+        const float kf = sf * (float)(0.5 / M_PI);
+        long long wind;
+        if (amin > 1e-12f && fabsf(kf - rintf(kf)) < 0.25f) {
+            wind = (long long)rintf(kf);
+        } else {
+            double s = 0.0;
+            for (int q = 0; q < 4; ++q) {
+                const int p0 = c[q], p1 = c[(q + 1) & 3];
+                const double ax = at(p0, 0), ay = at(p0, 1), bx = at(p1, 0), by = at(p1, 1);
+                const double cr = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
+                const double dt = __dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by));
+                s = __dadd_rn(s, atan2(cr, dt));
+            }
+            wind = llround(s / (2.0 * M_PI));
+        }
+        if (wind != 1) continue;
         const double z0 = at(t, 2), z1 = at(t + 1, 2), z2 = at(t + D, 2), z3 = at(t + D + 1, 2);
         double w = __dmul_rn(z0, z0);
         w = __dadd_rn(w, __dmul_rn(z1, z1));

@@ -440,8 +440,12 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
 
 // ----------------------------------------------------------- global path
 
+// Resident CTAs per SM the row passes are compiled for: at P = 1024 (FP32) a
+// cap of 80 registers leaves room for three CTAs of 256 threads, which the
+// latency-bound row loads need.
+template <int P, typename T> struct RowsMinB { static constexpr int v = (P == 1024 && sizeof(T) == 4) ? 3 : 1; };
 template <int P, typename T, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, RowsMinB<P, T>::v)
     k_g_rows(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ msbase,
              cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP, int inverse)
 {
