@@ -178,9 +178,11 @@ int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, co
  * m_i <- normalise(m_i/2 + e_i/(2|e_i|)).  Multipliers start at zero.  m is
  * updated in place.  Outputs (host arrays, any may be NULL): U_out[B] the
  * double-precision energy of the relaxed state (units of J), lambda_out[B][2],
- * iters_out[B] sweeps applied.  Runs on the on-chip kernel only (P <= 128 in
- * ND_FP32, P <= 64 in ND_FP64), otherwise ND_ERR_ARG.  Returns
- * ND_ERR_NOT_CONVERGED if a replica reached max_iter.  Synchronises `stream`. */
+ * iters_out[B] sweeps applied.  Size classes held on chip (P <= 128 in
+ * ND_FP32, P <= 64 in ND_FP64) relax in one launch; larger ones run the sweeps
+ * as grid-wide passes and check every 32 sweeps (a host synchronisation)
+ * whether all their replicas have converged.  Returns ND_ERR_NOT_CONVERGED if
+ * a replica reached max_iter.  Synchronises `stream`. */
 int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int max_iter, double *U_out,
                          double *lambda_out, int *iters_out, void *stream);
 

@@ -119,6 +119,7 @@ struct nd_handle {
     int *aux_i = nullptr;                 // [B * 2]
     RelaxIO *rio_d = nullptr;             // [B] relaxation inputs/outputs
     RelaxIO *rio_h = nullptr;             // pinned [B]
+    double *relax_part = nullptr;         // global-path relaxation partial sums [B][kRelaxBlocks][6]
     // statistics (device resident, filled by nd_stats_sample)
     StatsAcc *stats = nullptr;
     unsigned long long *hist_r = nullptr, *hist_v = nullptr;
@@ -541,6 +542,7 @@ void nd_destroy(nd_handle *h)
     cudaFree(h->aux_d);
     cudaFree(h->aux_i);
     cudaFree(h->rio_d);
+    cudaFree(h->relax_part);
     cudaFreeHost(h->rio_h);
     cudaFree(h->stats);
     cudaFree(h->hist_r);
@@ -724,13 +726,17 @@ int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int
     if (int rc = check_handle(h)) return rc;
     if (!X) return fail(ND_ERR_ARG, "null X");
     if (max_iter < 0 || !(tol > 0)) return fail(ND_ERR_ARG, "max_iter must be >= 0 and tol > 0");
-    for (auto &c : h->classes)
-        if (!c.fused_main)
-            return fail(ND_ERR_ARG, "relaxation runs on the on-chip kernel only (P <= 128 in FP32, P <= 64 in FP64)");
+    bool any_global = false;
+    for (auto &c : h->classes) any_global |= !c.fused_main;
     cudaStream_t st = (cudaStream_t)stream;
     void *md = nullptr;
     if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
     const int B = (int)h->rep_disk.size();
+    if (any_global) {
+        if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
+        if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
+        if (int rc = ensure_alloc((void **)&h->relax_part, sizeof(double) * 6 * kRelaxBlocks * (size_t)B)) return rc;
+    }
     ND_CUDA(cudaStreamSynchronize(st));   // the pinned relaxation block is rewritten below
     for (int r = 0; r < B; ++r) {
         const DiskInfo &d = h->disks[h->rep_disk[r]];
@@ -764,7 +770,18 @@ int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int
         a.tol = tol;
         a.rc2 = rcut * rcut;
         a.max_iter = max_iter;
-        ND_CUDA(launch_fused(c.P, prec, a));
+        if (c.fused_main) {
+            ND_CUDA(launch_fused(c.P, prec, a));
+        } else {
+            a.ms = h->ms;
+            a.spec = h->spec;
+            a.part = h->relax_part;
+            a.rio_host = h->rio_h;
+            a.n_rio = B;
+            a.work_host = c.reps.data();
+            a.n_sm = h->n_sm;
+            ND_CUDA(launch_global(c.P, prec, a, c.maxD));
+        }
     }
     ND_CUDA(cudaMemcpyAsync(h->rio_h, h->rio_d, sizeof(RelaxIO) * B, cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));

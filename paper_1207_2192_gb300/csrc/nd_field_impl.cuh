@@ -630,6 +630,125 @@ __global__ void k_g_load_stage(const Replica *__restrict__ reps, const int *__re
     }
 }
 
+// Constrained relaxation on the global path (Sec. IV; same sweep as the fused
+// kernel's relaxation mode): per iteration the field passes, then
+//   k_g_relax_reduce  per-block partial sums of the constraint values C_k, the
+//                     Jacobian J and the residual max |m x e|/|e| of the trial
+//                     alignment with the current multipliers,
+//   k_g_relax_newton  per replica: fixed-order total, convergence test, one
+//                     Newton step on the multipliers,
+//   k_g_relax_update  the damped alignment with the new multipliers.
+// Replicas that have converged (status 0) are left untouched.
+template <int P, typename T>
+__global__ void __launch_bounds__(256)
+    k_g_relax_reduce(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ msbase,
+                     const cplx<T> *__restrict__ specbase, const RelaxIO *__restrict__ rio, double rc2_d,
+                     double eta_d, double *__restrict__ part)
+{
+    constexpr int RS = SpecGeom<P>::RS;
+    __shared__ RelaxAcc<T> racc[8];
+    const int ridx = work[blockIdx.y], tid = threadIdx.x;
+    if (rio[ridx].status == 0) return;   // CTA-uniform
+    const Replica &r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const long long ms_s = (long long)D * r.Dpad, cs = (long long)D * RS;
+    const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off);
+    const V3Ptr<T> ms{const_cast<T *>(msbase) + r.state_off, ms_s};
+    const T relX = (T)rio[ridx].X[0], relY = (T)rio[ridx].X[1], l0 = (T)rio[ridx].lam[0], l1 = (T)rio[ridx].lam[1];
+    const T eta = (T)eta_d, rc2 = (T)rc2_d;
+    const StepParams<T> sp = step_params<T>(r);
+    RelaxAcc<T> a = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int cell = blockIdx.x * 256 + tid; cell < DD; cell += kRelaxBlocks * 256) {
+        if (!r.mask[cell]) continue;
+        const int y = cell / D, x = cell - y * D;
+        const long long si = (long long)y * r.Dpad + x, hi = (long long)y * (2 * RS) + x;
+        const vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+        const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+        relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, l0, l1, eta, a);
+    }
+    a.C0 = warp_sum_t(a.C0); a.C1 = warp_sum_t(a.C1); a.J00 = warp_sum_t(a.J00);
+    a.J01 = warp_sum_t(a.J01); a.J11 = warp_sum_t(a.J11); a.res = warp_max_t(a.res);
+    if ((tid & 31) == 0) racc[tid >> 5] = a;
+    __syncthreads();
+    if (tid == 0) {
+        RelaxAcc<T> t = racc[0];
+        for (int w = 1; w < 8; ++w) {
+            t.C0 += racc[w].C0; t.C1 += racc[w].C1; t.J00 += racc[w].J00; t.J01 += racc[w].J01;
+            t.J11 += racc[w].J11; t.res = max(t.res, racc[w].res);
+        }
+        double *o = part + ((size_t)ridx * kRelaxBlocks + blockIdx.x) * 6;
+        o[0] = t.C0; o[1] = t.C1; o[2] = t.J00; o[3] = t.J01; o[4] = t.J11; o[5] = t.res;
+    }
+}
+
+static __global__ void k_g_relax_newton(const int *__restrict__ work, int nwork, RelaxIO *__restrict__ rio,
+                                 const double *__restrict__ part, double tol, int iter)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    const int ridx = work[w];
+    RelaxIO &R = rio[ridx];
+    if (R.status == 0) return;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < kRelaxBlocks; ++b) {
+        const double *o = part + ((size_t)ridx * kRelaxBlocks + b) * 6;
+        for (int k = 0; k < 5; ++k) s[k] += o[k];
+        s[5] = fmax(s[5], o[5]);
+    }
+    R.resid = s[5];
+    if (s[5] < tol) {
+        R.status = 0;   // converged: iters keeps the number of sweeps applied
+        return;
+    }
+    const double det = s[2] * s[4] - s[3] * s[3];
+    if (det != 0.0 && isfinite(det)) {
+        R.lam[0] += -(s[4] * s[0] - s[3] * s[1]) / det;
+        R.lam[1] += -(-s[3] * s[0] + s[2] * s[1]) / det;
+    }
+    R.iters = iter + 1;
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256)
+    k_g_relax_update(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ msbase,
+                     const cplx<T> *__restrict__ specbase, const RelaxIO *__restrict__ rio, double rc2_d, double eta_d)
+{
+    constexpr int RS = SpecGeom<P>::RS;
+    const int ridx = work[blockIdx.y];
+    if (rio[ridx].status == 0) return;
+    const Replica &r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const int cell = blockIdx.x * 256 + threadIdx.x;
+    if (cell >= DD || !r.mask[cell]) return;
+    const long long ms_s = (long long)D * r.Dpad, cs = (long long)D * RS;
+    const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off);
+    V3Ptr<T> ms{msbase + r.state_off, ms_s};
+    const T relX = (T)rio[ridx].X[0], relY = (T)rio[ridx].X[1], m0 = (T)rio[ridx].lam[0], m1 = (T)rio[ridx].lam[1];
+    const StepParams<T> sp = step_params<T>(r);
+    const int y = cell / D, x = cell - y * D;
+    const long long si = (long long)y * r.Dpad + x, hi = (long long)y * (2 * RS) + x;
+    const vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+    RelaxAcc<T> dummy = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < (T)rc2_d, dx, dy, m0, m1, (T)eta_d, dummy));
+}
+
+// The stage buffer back to the caller's state (cells inside the disk).
+template <typename T>
+__global__ void k_g_store_stage(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ msbase,
+                                T *__restrict__ ybase)
+{
+    const Replica &r = reps[work[blockIdx.y]];
+    const int D = r.D, DD = D * D;
+    const long long ms_s = (long long)D * r.Dpad;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < DD; cell += gridDim.x * blockDim.x) {
+        if (!r.mask[cell]) continue;
+        const int y = cell / D, x = cell - y * D;
+        const long long si = r.state_off + (long long)y * r.Dpad + x;
+        for (int c = 0; c < 3; ++c) ybase[si + c * ms_s] = msbase[si + c * ms_s];
+    }
+}
+
 // --------------------------------------------------------- launch helpers
 
 
@@ -759,9 +878,10 @@ static void launch_g_epi(const LaunchArgs &a, dim3 ge, int stage, unsigned long 
                                                    (const cplx<T> *)a.spec, a.red, stage, step);
 }
 
-// One field evaluation on the global path: stage buffer -> spectrum -> field.
+// The three FFT passes of one field evaluation on the global path: stage
+// buffer -> spectrum -> field rows (in the spectrum buffer).
 template <int P, typename T>
-static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode, unsigned long long step)
+static void glob_field_passes(const LaunchArgs &a, int maxD)
 {
     constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
     const int nrow = row_tasks(maxD);
@@ -778,6 +898,13 @@ static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode,
         k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
     }
     k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 1);
+}
+
+// One field evaluation on the global path with its epilogue.
+template <int P, typename T>
+static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode, unsigned long long step)
+{
+    glob_field_passes<P, T>(a, maxD);
     dim3 ge((maxD * maxD + 255) / 256, a.nwork);
     switch (mode) {
     case M_FIELD: launch_g_epi<P, T, M_FIELD>(a, ge, stage, step); break;
@@ -807,6 +934,33 @@ static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
     k_g_load_stage<T><<<gl, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.y, (T *)a.ms);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (a.mode == M_RELAX) {
+        if (!a.rio || !a.part || !a.rio_host || !a.work_host) return cudaErrorInvalidValue;
+        const dim3 gp(kRelaxBlocks, a.nwork), gu((maxD * maxD + 255) / 256, a.nwork);
+        constexpr int kCheck = 32;   // iterations between host checks for convergence of every replica
+        for (int it = 0; it < a.max_iter; ++it) {
+            glob_field_passes<P, T>(a, maxD);
+            k_g_relax_reduce<P, T><<<gp, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.ms, (const cplx<T> *)a.spec,
+                                                             a.rio, a.rc2, a.eta, a.part);
+            k_g_relax_newton<<<(a.nwork + 127) / 128, 128, 0, a.stream>>>(a.work, a.nwork, a.rio, a.part, a.tol, it);
+            k_g_relax_update<P, T><<<gu, 256, 0, a.stream>>>(a.reps, a.work, (T *)a.ms, (const cplx<T> *)a.spec, a.rio,
+                                                             a.rc2, a.eta);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((it + 1) % kCheck == 0 || it + 1 == a.max_iter) {
+                // a synchronous read of the parameter array; stop once every
+                // replica of this launch has converged
+                if ((e = cudaMemcpyAsync(a.rio_host, a.rio, sizeof(RelaxIO) * a.n_rio, cudaMemcpyDeviceToHost,
+                                         a.stream)) != cudaSuccess)
+                    return e;
+                if ((e = cudaStreamSynchronize(a.stream)) != cudaSuccess) return e;
+                bool running = false;
+                for (int k = 0; k < a.nwork && !running; ++k) running = a.rio_host[a.work_host[k]].status != 0;
+                if (!running) break;
+            }
+        }
+        k_g_store_stage<T><<<gl, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.ms, (T *)a.y);
+        return cudaGetLastError();
+    }
     const int nst = (a.mode == M_RK4) ? 4 : (a.mode == M_HEUN ? 2 : 1);
     const long long nsteps = (a.mode == M_FIELD || a.mode == M_ENERGY) ? 1 : a.nsteps;
     for (long long n = 0; n < nsteps; ++n)

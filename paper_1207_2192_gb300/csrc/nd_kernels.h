@@ -32,6 +32,10 @@ struct LaunchArgs {
     cudaStream_t stream = 0;
     // relaxation
     RelaxIO *rio = nullptr;          // per replica, indexed like reps
+    RelaxIO *rio_host = nullptr;     // host copy of the same array (global-path convergence checks)
+    int n_rio = 0;                   // entries of rio
+    const int *work_host = nullptr;  // host copy of work (nwork entries)
+    double *part = nullptr;          // global-path relaxation partial sums: [replicas][kRelaxBlocks][6]
     double eta = 0.5, tol = 1e-6, rc2 = 0.0;
     int max_iter = 0;
     // time-sliced schedule (fused steppers): ncta CTAs run the segments
@@ -46,6 +50,8 @@ struct LaunchArgs {
     int variant = 0;                 // fused-kernel thread-count variant (stepping modes)
     int n_sm = 1;                    // multiprocessors of the device (persistent grids)
 };
+
+constexpr int kRelaxBlocks = 64;    // global-path relaxation: partial-sum blocks per replica
 
 struct SegmentHost {                 // mirrors Segment in nd_field_impl.cuh
     int rep, wait, signal, pad;

@@ -67,8 +67,52 @@ def test_relaxed_energies_and_kF_match_oracle(O):
         assert np.all(st == 0) and abs(Xc[1, 0] - 2 * a) < 0.1 * a
 
 
-def test_relax_rejects_global_path_sizes():
-    h = Nanodisk([Disk(70e-9, 12e-9)], [1], nd.ND_FP32)     # P = 256
+@pytest.mark.parametrize("prec,tol,disks", [
+    (nd.ND_FP32, 2e-5, [(66e-9, 10e-9)]),                  # P = 256: global path
+    (nd.ND_FP64, 1e-11, [(40e-9, 10e-9)]),                 # P = 128 in FP64: global path
+    (nd.ND_FP32, 2e-5, [(30e-9, 10e-9), (66e-9, 10e-9)]),  # one fused and one global size class
+])
+def test_global_path_relax_sweeps_match_oracle(O, prec, tol, disks):
+    """The relaxation sweeps of the global path (sizes the on-chip kernel does
+    not hold) against the oracle sweep by sweep, in a handle that may mix size
+    classes."""
+    nsweep = 3
+    ds = [Disk(R, L) for R, L in disks]
+    h = Nanodisk(ds, [2] * len(ds), prec)
+    X = np.array([[2.5e-9, 1.0e-9], [0.0, -2e-9]] * len(ds))
+    grids = []
+    for d in ds:
+        model = model_for(O, d)
+        grids += [model.init_vortex(0.0, 0.0), model.init_vortex(-1e-9, 2e-9)]
+    m = h.to_device(grids)
+    rc, U, lam, it = h.relax(m, X, tol=1e-300, max_iter=nsweep)
+    assert rc == nd.ND_ERR_NOT_CONVERGED and np.all(it == nsweep)
+    out = h.unpack(m)
+    start = h.unpack(h.to_device(grids))
+    for r in range(h.B):
+        model = model_for(O, ds[h.rep_disk[r]])
+        mm, lm = start[r], np.zeros(2)
+        for _ in range(nsweep):
+            mm, lm, _ = model.relax_sweep(mm, X[r], lm)
+        assert np.max(np.abs(out[r] - mm)) < 10 * tol
+        assert np.allclose(lam[r], lm, rtol=100 * tol, atol=100 * tol * max(1e-3, np.abs(lm).max()))
+        assert U[r] == pytest.approx(model.energy(out[r]), rel=1e-12)
+
+
+def test_global_path_relax_converges_to_oracle_energy(O):
+    """A converged FP64 relaxation on the global path (P = 128 in FP64) ends at
+    the oracle's energy and multipliers, and stops early: every replica reports
+    its own sweep count below max_iter."""
+    disk = Disk(40e-9, 10e-9)
+    model = model_for(O, disk)
+    X = np.array([3e-9, 0.0])
+    ref = model.relax(model.init_vortex(*X), X, tol=1e-9, max_iter=20000)
+    assert ref["status"] == 0
+    h = Nanodisk([disk], [1], nd.ND_FP64)
     m = h.empty_device()
-    with pytest.raises(nd.NDError):
-        h.relax(m, [[0.0, 0.0]], max_iter=1)
+    h.init_vortex(m, X.reshape(1, 2))
+    rc, U, lam, it = h.relax(m, X.reshape(1, 2), tol=1e-9, max_iter=20000)
+    assert rc == nd.ND_OK
+    assert 0 < it[0] < 20000 and abs(int(it[0]) - ref["iters"]) <= 1
+    assert U[0] == pytest.approx(ref["U"], rel=1e-9)
+    assert np.allclose(lam[0], ref["lam"], rtol=1e-5, atol=1e-8)
