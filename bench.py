@@ -59,12 +59,22 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152, lanes=128):
     return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
 
 
-def kernel_sources_sha256():
-    """Hash of the CUDA sources (changes whenever a kernel changes)."""
+# The sources that make up each workload's dominant kernel: its translation
+# unit and the headers it includes.
+KERNEL_SOURCES = {
+    "batched_heun": ["nd_fused_f32.cu", "nd_field_impl.cuh", "nd_phases.cuh", "nd_fft.cuh", "nd_common.cuh", "nd_kernels.h"],
+    "large_disk": ["nd_glob_f32.cu", "nd_field_impl.cuh", "nd_phases.cuh", "nd_fft.cuh", "nd_common.cuh", "nd_kernels.h"],
+}
+KERNEL_SOURCES["plain"] = KERNEL_SOURCES["batched_heun"]
+
+
+def kernel_sources_sha256(workload="batched_heun"):
+    """Hash of the CUDA sources of the workload's dominant kernel (changes
+    whenever that kernel changes)."""
     import hashlib
     d = os.path.join(ROOT, "paper_1207_2192_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES[workload]:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
@@ -72,15 +82,14 @@ def kernel_sources_sha256():
 
 def profiled_traffic(workload):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None if the kernels changed since it was captured."""
+    summary, or None if that kernel's sources changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     if not os.path.exists(p):
         return None
-    rec = json.load(open(p))
-    if rec.get("sources_sha256") != kernel_sources_sha256():
+    e = json.load(open(p)).get("entries", {}).get(workload)
+    if e is None or e.get("sources_sha256") != kernel_sources_sha256(workload):
         return None
-    e = rec.get("entries", {}).get(workload)
-    return None if e is None else e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_launch")
 
 
 def measured_peaks():
@@ -307,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
             peak = peaks.get("hbm_gbs", 6800.0)
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": profiled_traffic(args.workload),
-                    "kernel": "global-path Heun step (k_g_rows, k_g_cols, k_g_epi)",
+                    "kernel": "global-path Heun step (k_g_rows, k_g_cols_split, k_g_epi)",
                     "bytes_per_cell_update": nbytes_step / wl.cell_updates_per_step(),
                     "peak_note": "measured copy bandwidth, MEASURED_PEAKS.json",
                     "timing": "CUDA events around nd_step_heun on the bench stream, 5 launches, L2 flushed"}

@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NT, RowsMinB<P, T>::v)
         row_fwd_task<P, T>(q, q < nrow, D, msbase + r.state_off, r.Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw,
                            gid.gmask);
     } else {
-        row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+        row_inv_task<P, T, true>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
     }
 }
 

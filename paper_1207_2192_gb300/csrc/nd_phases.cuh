@@ -284,7 +284,10 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
 
 // ---------------------------------------------------------------- row inv
 
-template <int P, typename T>
+// HALF_LOAD: read only the stored half rows k <= P/2 and take the mirrored
+// entries k > P/2 from the group's scratch (for spectra in global memory,
+// where each load is a round trip to L2; on chip the direct reads are cheaper).
+template <int P, typename T, bool HALF_LOAD = false>
 __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> *spec, long long cstride, int t,
                                              cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
 {
@@ -297,18 +300,47 @@ __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> 
     cplx<T> *rA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
     cplx<T> *rB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
     cplx<T> v[R1];
+    if constexpr (HALF_LOAD) {
+        static_assert(Gm::SCRATCH >= P + 2, "scratch holds both half rows");
+        constexpr int KB = P / 2 + 1;   // B's half row starts here in the scratch
 #pragma unroll
-    for (int o = 0; o < R1; ++o) {
-        const int k = t + G * o;
-        const bool up = k <= P / 2;
-        const int kk = up ? k : P - k;
-        cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
-        if (active) {
-            a = rA[kk];
-            if (hasB) b = rB[kk];
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            if (k <= P / 2) {
+                cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
+                if (active) {
+                    a = rA[k];
+                    if (hasB) b = rB[k];
+                }
+                scr[k] = a;
+                scr[KB + k] = b;
+                v[o] = {a.x - b.y, a.y + b.x};
+            }
         }
-        if (!up) { a.y = -a.y; b.y = -b.y; }
-        v[o] = {a.x - b.y, a.y + b.x};
+        __syncwarp(gmask);
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            if (k > P / 2) {
+                const cplx<T> a = scr[P - k], b = scr[KB + P - k];
+                v[o] = {a.x + b.y, -a.y + b.x};   // conj(a) + i conj(b)
+            }
+        }
+        __syncwarp(gmask);
+    } else {
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            const bool up = k <= P / 2;
+            const int kk = up ? k : P - k;
+            cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
+            if (active) {
+                a = rA[kk];
+                if (hasB) b = rB[kk];
+            }
+            if (!up) { a.y = -a.y; b.y = -b.y; }
+            v[o] = {a.x - b.y, a.y + b.x};
+        }
     }
     fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
     if (!active) return;
