@@ -193,6 +193,16 @@ int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int
  * flagged non-finite values, else ND_OK.  The paper has no counterpart. */
 int nd_check_status(nd_handle *h, void *stream);
 
+/* Failure-path self-test of the time-sliced schedule: launches the stepping
+ * kernel as one CTA with one segment that waits for a replica hand-over flag
+ * that no segment ever sets.  The wait is bounded (about one second of
+ * polling); when it expires the kernel sets ND_DEV_TIMEOUT in the handle's
+ * status word and returns without reading or writing any state, so the
+ * context stays usable and the next nd_check_status returns ND_ERR_TIMEOUT.
+ * Synchronises `stream`.  Needs an ND_FP32 handle whose first size class is
+ * held on chip (P <= 128), else ND_ERR_ARG.  The paper has no counterpart. */
+int nd_selftest_handover_timeout(nd_handle *h, void *stream);
+
 /* Analytic q = +1 vortex centred at X0[r] = (x0, y0) metres (host array
  * [B][2]) for every replica (Sec. IV profile): in-plane angle atan2(y - y0,
  * x - x0) + chirality pi/2, m_z = polarity exp(-rho^2/lambda_ex^2), |m| = 1. */

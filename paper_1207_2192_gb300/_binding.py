@@ -62,6 +62,7 @@ SIGNATURES = {
     "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
     "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
     "nd_check_status": (_I, [_P, _P]),
+    "nd_selftest_handover_timeout": (_I, [_P, _P]),
     "nd_graph_create": (_I, [_P, _P, _I, _LL, _D, _P, _P, _ULL, _I, _P]),
     "nd_autotune": (_I, [_P, _I, _D, _LL, _P]),
     "nd_set_plan": (_I, [_P, _I, _I, _I]),
@@ -265,6 +266,11 @@ def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
 def nd_check_status(h, stream=None):
     """Synchronise and return the device status code (ND_OK, ND_ERR_TIMEOUT, ND_ERR_NAN)."""
     return lib().nd_check_status(h, _stream(stream))
+
+
+def nd_selftest_handover_timeout(h, stream=None):
+    """Run the bounded-wait failure path once (see include/nanodisk.h)."""
+    _check(lib().nd_selftest_handover_timeout(h, _stream(stream)))
 
 
 def nd_graph_create(h, m, method, n_steps, dt_seconds, T_kelvin=None, seed=None, step0=0, stats_sample=False):

@@ -878,6 +878,50 @@ int nd_check_status(nd_handle *h, void *stream)
     return ND_OK;
 }
 
+int nd_selftest_handover_timeout(nd_handle *h, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    auto &c = h->classes[0];
+    if (!c.fused_main || h->prec == ND_FP64)
+        return fail(ND_ERR_ARG, "the hand-over self-test needs an on-chip FP32 size class first in the handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    // one CTA, one segment of one step that waits for replica c.reps[0]'s flag,
+    // which no segment signals
+    const SegmentHost seg = {c.reps[0], 1, 0, 0, 0, 1};
+    const int off[2] = {0, 1};
+    void *segs_d = nullptr, *off_d = nullptr;
+    ND_CUDA(cudaMalloc(&segs_d, sizeof(seg)));
+    cudaError_t e = cudaMalloc(&off_d, sizeof(off));
+    if (e == cudaSuccess) e = cudaMemcpy(segs_d, &seg, sizeof(seg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(off_d, off, sizeof(off), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags_d, 0, sizeof(int) * h->rep_disk.size(), st);
+    if (e == cudaSuccess) {
+        LaunchArgs a;
+        a.mode = M_HEUN;
+        a.reps = h->reps_d;
+        a.work = c.work_d;
+        a.nwork = (int)c.reps.size();
+        a.y = h->acc;     // never touched: the segment gives up before reading any state
+        a.acc = h->acc;
+        a.tw = h->tw32[c.P];
+        a.nsteps = 1;
+        a.smem = c.smem_main;
+        a.stream = st;
+        a.status = h->status_d;
+        a.segs = segs_d;
+        a.seg_off = (const int *)off_d;
+        a.flags = h->flags_d;
+        a.ncta = 1;
+        a.n_sm = h->n_sm;
+        e = launch_fused(c.P, ND_PREC_FP32, a);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(segs_d);
+    cudaFree(off_d);
+    if (e != cudaSuccess) return fail(ND_ERR_CUDA, std::string("hand-over self-test: ") + cudaGetErrorString(e));
+    return ND_OK;
+}
+
 int nd_stats_reset(nd_handle *h, double r_max, int r_bins, double v_max, int v_bins)
 {
     if (int rc = check_handle(h)) return rc;

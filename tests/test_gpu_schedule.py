@@ -40,3 +40,26 @@ def test_time_sliced_schedule_is_bit_identical(mode):
     n0 = ms[0].numel()
     assert torch.equal(m[:n0], ms[0]) and torch.equal(m[n0:], ms[1])
     assert not torch.equal(m[:n0], parts[0].to_device(parts[0].unpack(ms[0])) * 0)
+
+
+def test_expired_handover_wait_reports_timeout_and_leaves_context_usable():
+    """A segment whose hand-over flag is never set gives up after its bounded
+    wait: the status word reports ND_ERR_TIMEOUT, no state is touched, and the
+    same handle steps normally afterwards."""
+    import time
+    h = Nanodisk([Disk(50e-9, 10e-9, alpha=0.01)], [3], nd.ND_FP32)
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((3, 2)))
+    before = m.clone()
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    t0 = time.perf_counter()
+    nd.nd_selftest_handover_timeout(h.h)
+    waited = time.perf_counter() - t0
+    assert nd.nd_check_status(h.h) == nd.ND_ERR_TIMEOUT
+    assert nd.nd_check_status(h.h) == nd.ND_OK          # reading the word clears it
+    assert 0.05 < waited < 30.0
+    assert torch.equal(m, before)
+    h.heun(m, 3, 1e-14, np.full(3, 300.0), np.arange(3, dtype=np.uint64))
+    torch.cuda.synchronize()
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    assert not torch.equal(m, before) and torch.isfinite(m).all()
