@@ -304,6 +304,9 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
             if (!a.ms || !a.spec) return fail(ND_ERR_ARG, "global-path buffers are not allocated");
             ND_CUDA(launch_global(c.P, prec, a, c.maxD));
         }
+        // a stepped state with a non-finite cell sets the NaN bit of the status word
+        if (mode == M_RK4 || mode == M_HEUN)
+            ND_CUDA(launch_check_finite(prec, a.reps, c.work_d, (int)c.reps.size(), c.maxD, y, h->status_d, st));
     }
     return ND_OK;
 }

@@ -484,21 +484,33 @@ cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cu
     return cudaGetLastError();
 }
 
+// Sets ND_DEV_NAN in *flag if any component of a cell inside a disk is not
+// finite (cells outside the disks and padding columns are ignored).
+// grid = (cell blocks, replicas).
 template <typename T>
-__global__ void k_check_finite(const T *y, size_t n, unsigned *flag)
+__global__ void k_check_finite(const Replica *reps, const int *work, const T *ybase, unsigned *flag)
 {
+    const Replica &r = reps[work[blockIdx.y]];
+    const int D = r.D, DD = D * D;
+    const long long cs = (long long)D * r.Dpad;
     bool bad = false;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        bad |= !isfinite((double)y[i]);
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < DD; cell += gridDim.x * blockDim.x) {
+        if (!r.mask[cell]) continue;
+        const int j = cell / D, i = cell - j * D;
+        const T *y = ybase + r.state_off + (long long)j * r.Dpad + i;
+        bad |= !(isfinite(y[0]) && isfinite(y[cs]) && isfinite(y[2 * cs]));
+    }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, ND_DEV_NAN);
 }
 
-cudaError_t launch_check_finite(int prec, const void *y, size_t n, unsigned *flag, cudaStream_t st)
+cudaError_t launch_check_finite(int prec, const Replica *reps, const int *work, int nwork, int maxD, const void *y,
+                                unsigned *flag, cudaStream_t st)
 {
-    const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
-    if (n == 0) return cudaSuccess;
-    if (prec == ND_PREC_FP64) k_check_finite<double><<<blocks, 256, 0, st>>>((const double *)y, n, flag);
-    else k_check_finite<float><<<blocks, 256, 0, st>>>((const float *)y, n, flag);
+    if (nwork == 0) return cudaSuccess;
+    const int cells = maxD * maxD, bx = (cells + 255) / 256 < 64 ? (cells + 255) / 256 : 64;
+    dim3 g(bx, nwork);
+    if (prec == ND_PREC_FP64) k_check_finite<double><<<g, 256, 0, st>>>(reps, work, (const double *)y, flag);
+    else k_check_finite<float><<<g, 256, 0, st>>>(reps, work, (const float *)y, flag);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ cudaError_t launch_advance_steps(Replica *reps, int n, long long steps, cudaStre
 cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y,
                           double *out /*[nrep][3]*/, cudaStream_t st);
 cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st);
-cudaError_t launch_check_finite(int prec, const void *y, size_t n, unsigned *flag, cudaStream_t st);
+cudaError_t launch_check_finite(int prec, const Replica *reps, const int *work, int nwork, int maxD, const void *y,
+                                unsigned *flag, cudaStream_t st);
 
 }  // namespace nd

@@ -71,3 +71,51 @@ def test_large_disk_heun_properties():
         n = np.sqrt((g[r] ** 2).sum(0))[mask]
         assert np.max(np.abs(n - 1)) < 1e-5
     assert not np.allclose(g[0], g[1])
+
+
+def test_uneven_batch_full_size_with_graphs_and_autotuned_plans(O):
+    """The uneven batch: 64 disks with R ~ U(20, 100) nm, L/R ~ U(0.05, 0.2)
+    and T ~ U(0, 400) K, disks 0-7 at T = 0 stepping with RK4 and the rest
+    with Heun, size classes P = 64, 128 and 256 (on-chip and global paths).
+    Each method's handle is autotuned and its steps captured in one CUDA
+    graph; sampled disks of every size class match their oracle trajectory."""
+    R, L, T = ndsynth.uneven_disks(64, seed=0)
+    alpha, dt, steps = 0.01, 1e-14, 2
+    groups = {"rk4": list(range(8)), "heun": list(range(8, 64))}
+    hs, ms, starts = {}, {}, {}
+    for name, idx in groups.items():
+        h = Nanodisk([Disk(R[i], L[i], alpha=alpha) for i in idx], None, nd.ND_FP32)
+        method = nd.ND_METHOD_RK4 if name == "rk4" else nd.ND_METHOD_HEUN
+        nd.nd_autotune(h.h, method, dt, n_steps=4)
+        m = h.empty_device()
+        h.init_vortex(m, np.stack([0.1 * R[idx], np.zeros(len(idx))], 1))
+        starts[name] = h.unpack(m)
+        Tk = T[idx] if name == "heun" else None
+        seeds = np.arange(len(idx), dtype=np.uint64) + 100 if name == "heun" else None
+        g = nd.nd_graph_create(h.h, m, method, steps, dt, Tk, seeds, step0=0)
+        nd.nd_graph_launch(g)
+        nd.nd_graph_destroy(g)
+        hs[name], ms[name] = h, m
+    Ps = {name: sorted({hs[name].layout[r]["P"] for r in range(hs[name].B)}) for name in groups}
+    assert Ps["heun"][0] <= 64 and Ps["heun"][-1] == 256
+    for name, idx in groups.items():
+        h = hs[name]
+        assert nd.nd_check_status(h.h) == nd.ND_OK
+        out = h.unpack(ms[name])
+        Pk = [h.layout[r]["P"] for r in range(h.B)]
+        # one replica of every size class, plus the largest disk
+        pick = sorted({Pk.index(p) for p in set(Pk)} | {int(np.argmax(R[idx]))})
+        for r in pick:
+            i = idx[r]
+            model = O.Model(R[i], L[i], alpha=alpha)
+            if name == "rk4":
+                ref = model.rk4(starts[name][r], steps, model.dtau(dt))
+            else:
+                Ts = O.scaled_temperature(T[i], model.A, model.L)
+                ref = model.heun(starts[name][r], steps, model.dtau(dt), Ts, 100 + r, 0)
+            assert np.max(np.abs(out[r] - ref)) < 1e-4, (name, r, Pk[r])
+            # relative to the change over the run, plus the FP32 rounding of the
+            # stored state itself (~1e-7 per component, rms over 3C components)
+            change = np.linalg.norm((ref - starts[name][r]) * model.mask)
+            floor = 1e-7 * np.sqrt(3 * model.C)
+            assert np.linalg.norm((out[r] - ref) * model.mask) <= 2e-4 * change + floor, (name, r, Pk[r])

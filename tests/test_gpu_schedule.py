@@ -63,3 +63,26 @@ def test_expired_handover_wait_reports_timeout_and_leaves_context_usable():
     torch.cuda.synchronize()
     assert nd.nd_check_status(h.h) == nd.ND_OK
     assert not torch.equal(m, before) and torch.isfinite(m).all()
+
+
+def test_non_finite_state_sets_the_nan_status():
+    """A NaN in a disk cell propagates through a step and the status word
+    reports ND_ERR_NAN; a NaN outside the disk is ignored."""
+    disk = Disk(30e-9, 10e-9, alpha=0.01)
+    h = Nanodisk([disk], [2], nd.ND_FP32)
+    mask = h.mask(0).astype(bool)
+    D = h.layout[0]["D"]
+    g = [np.zeros((3, D, D)) for _ in range(2)]
+    for k in range(2):
+        g[k][2][mask] = 1.0
+    outside = np.argwhere(~mask)[0]
+    g[0][0, outside[0], outside[1]] = np.nan            # ignored: not a disk cell
+    m = h.to_device(g)
+    h.rk4(m, 1, 1e-14)
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    inside = np.argwhere(mask)[len(np.argwhere(mask)) // 2]
+    g[1][1, inside[0], inside[1]] = np.nan
+    m = h.to_device(g)
+    h.rk4(m, 1, 1e-14)
+    assert nd.nd_check_status(h.h) == nd.ND_ERR_NAN
+    assert nd.nd_check_status(h.h) == nd.ND_OK
