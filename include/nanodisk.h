@@ -239,6 +239,36 @@ int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, uns
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Time series of the average magnetisation and their power spectra (Sec. V:
+ * the thermal power spectra of <m_x> whose peaks give the gyrotropic
+ * frequency and the higher modes).
+ *
+ * nd_series_reset allocates, for every replica, room for `capacity` samples
+ * of <m> = (<m_x>, <m_y>, <m_z>) (double precision, averages over the disk
+ * cells) and zeroes the device sample counter.  nd_series_sample appends one
+ * sample of every replica at the counter's index and advances it (samples
+ * past capacity are dropped; graph replays can append, see ND_GRAPH_SERIES).
+ * nd_series_read synchronises the device and reports the number of samples
+ * taken (n_samples, which may exceed capacity) and, if out is not NULL, copies
+ * the kept ones, min(n_samples, capacity) per replica, to out
+ * [B][kept][3].
+ *
+ * nd_power_spectrum splits each replica's kept series of one component
+ * (0 = x, 1 = y, 2 = z) into n_windows = kept / window non-overlapping windows
+ * (window 64, 128, 256, 512 or 1024 samples), removes each window's mean, and
+ * returns the averaged one-sided periodogram
+ *   psd_out[r][k] = (2 or 1) (dt_sample / window) < |sum_t x_t e^{-2 pi i k t/window}|^2 >_windows,
+ * k = 0..window/2 (factor 2 except at k = 0 and window/2), in (units of
+ * <m>)^2 per hertz, with freq_out[k] = k / (window dt_sample) hertz.  psd_out
+ * is a host array [B][window/2+1], freq_out [window/2+1] (either may be NULL).
+ * ND_ERR_ARG if fewer than `window` samples are kept.  Synchronises `stream`. */
+int nd_series_reset(nd_handle *h, int capacity);
+int nd_series_sample(nd_handle *h, const void *m, void *stream);
+int nd_series_read(nd_handle *h, double *out, long long *n_samples);
+int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_seconds, double *psd_out,
+                      double *freq_out, int *n_windows, void *stream);
+
+/* ------------------------------------------------------------------------
  * Autotuning of the stepping schedule.  The replicas of a handle are grouped
  * by padded FFT size P ("size classes"); each class can step on the fused
  * on-chip kernel with one of up to three thread counts (which set how many
@@ -263,8 +293,10 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
 /* ------------------------------------------------------------------------
  * Graph-captured stepping.  nd_graph_create records, once, the whole launch
  * sequence of n_steps RK4 or Heun steps of every replica of the handle on
- * the device state m (plus, if stats_sample, one nd_stats_sample) as a CUDA
- * graph; the noise-step counter lives on the device and advances by n_steps
+ * the device state m, followed by the samples that the flags in stats_sample
+ * select (ND_GRAPH_STATS: one nd_stats_sample; ND_GRAPH_SERIES: one
+ * nd_series_sample), as a CUDA graph; the noise-step counter lives on the
+ * device and advances by n_steps
  * at the end of every replay, so consecutive nd_graph_launch calls continue
  * the Philox stream exactly as nd_step_heun with step0 advanced would (the
  * trajectories are bit-identical).  The graph keeps its own copy of the
@@ -274,6 +306,8 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
  * (it is the batching of Sec. III's integrators).  nd_graph_nodes reports
  * the number of kernel nodes of one replay. */
 typedef struct nd_graph nd_graph;
+#define ND_GRAPH_STATS 1
+#define ND_GRAPH_SERIES 2
 int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double dt_seconds, const double *T_kelvin,
                     const unsigned long long *seed, unsigned long long step0, int stats_sample, nd_graph **out);
 int nd_graph_launch(nd_graph *g, void *stream);

@@ -71,6 +71,10 @@ SIGNATURES = {
     "nd_graph_nodes": (_I, [_P, _P]),
     "nd_graph_destroy": (None, [_P]),
     "nd_stats_sample": (_I, [_P, _P, _D, _P]),
+    "nd_series_reset": (_I, [_P, _I]),
+    "nd_series_sample": (_I, [_P, _P, _P]),
+    "nd_series_read": (_I, [_P, _P, _P]),
+    "nd_power_spectrum": (_I, [_P, _I, _I, _D, _P, _P, _P, _P]),
     "nd_stats_read": (_I, [_P, _P, _P, _P, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
 }
@@ -263,6 +267,36 @@ def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
     return mom, hr, hv
 
 
+def nd_series_reset(h, capacity):
+    _check(lib().nd_series_reset(h, int(capacity)))
+
+
+def nd_series_sample(h, m, stream=None):
+    _check(lib().nd_series_sample(h, _ptr(m), _stream(stream)))
+
+
+def nd_series_read(h, nrep, capacity):
+    """Returns (samples taken, array [nrep][kept][3] of the kept ones)."""
+    n = ctypes.c_longlong()
+    _check(lib().nd_series_read(h, None, ctypes.byref(n)))
+    kept = min(n.value, capacity)
+    out = np.zeros((nrep, kept, 3))
+    if kept:
+        _check(lib().nd_series_read(h, _ptr(out), ctypes.byref(n)))
+    return n.value, out
+
+
+def nd_power_spectrum(h, nrep, component, window, dt_sample_seconds, stream=None):
+    """Averaged one-sided periodogram of the recorded <m> series: returns
+    (psd [nrep][window/2+1], freq [window/2+1] in Hz, n_windows)."""
+    psd = np.zeros((nrep, window // 2 + 1))
+    freq = np.zeros(window // 2 + 1)
+    nw = ctypes.c_int()
+    _check(lib().nd_power_spectrum(h, int(component), int(window), float(dt_sample_seconds), _ptr(psd), _ptr(freq),
+                                   ctypes.byref(nw), _stream(stream)))
+    return psd, freq, nw.value
+
+
 def nd_check_status(h, stream=None):
     """Synchronise and return the device status code (ND_OK, ND_ERR_TIMEOUT, ND_ERR_NAN)."""
     return lib().nd_check_status(h, _stream(stream))
@@ -273,7 +307,12 @@ def nd_selftest_handover_timeout(h, stream=None):
     _check(lib().nd_selftest_handover_timeout(h, _stream(stream)))
 
 
+ND_GRAPH_STATS = 1
+ND_GRAPH_SERIES = 2
+
+
 def nd_graph_create(h, m, method, n_steps, dt_seconds, T_kelvin=None, seed=None, step0=0, stats_sample=False):
+    """stats_sample: False/True, or a combination of ND_GRAPH_STATS and ND_GRAPH_SERIES."""
     T = None if T_kelvin is None else np.ascontiguousarray(T_kelvin, dtype=np.float64)
     s = None if seed is None else np.ascontiguousarray(seed, dtype=np.uint64)
     g = ctypes.c_void_p()

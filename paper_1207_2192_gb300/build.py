@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnanodisk.so")
-SOURCES = ["nd_fused_f32.cu", "nd_fused_f64.cu", "nd_glob_f32.cu", "nd_glob_f64.cu", "nd_dispatch.cu", "nd_aux.cu", "nd_api.cu", "nd_noalloc.cu"]
+SOURCES = ["nd_fused_f32.cu", "nd_fused_f64.cu", "nd_glob_f32.cu", "nd_glob_f64.cu", "nd_dispatch.cu", "nd_aux.cu", "nd_api.cu", "nd_noalloc.cu", "nd_spectra.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -120,6 +120,11 @@ struct nd_handle {
     RelaxIO *rio_d = nullptr;             // [B] relaxation inputs/outputs
     RelaxIO *rio_h = nullptr;             // pinned [B]
     double *relax_part = nullptr;         // global-path relaxation partial sums [B][kRelaxBlocks][6]
+    double *series = nullptr;             // <m> time series [B][series_cap][3]
+    unsigned long long *series_count = nullptr;   // device sample counter
+    int series_cap = 0;
+    double *psd_work = nullptr;           // per-window periodograms
+    size_t psd_work_doubles = 0;
     // statistics (device resident, filled by nd_stats_sample)
     StatsAcc *stats = nullptr;
     unsigned long long *hist_r = nullptr, *hist_v = nullptr;
@@ -546,6 +551,9 @@ void nd_destroy(nd_handle *h)
     cudaFree(h->aux_i);
     cudaFree(h->rio_d);
     cudaFree(h->relax_part);
+    cudaFree(h->series);
+    cudaFree(h->series_count);
+    cudaFree(h->psd_work);
     cudaFreeHost(h->rio_h);
     cudaFree(h->stats);
     cudaFree(h->hist_r);
@@ -1006,6 +1014,110 @@ int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream)
     return ND_OK;
 }
 
+// ---------------------------------------------------------- time series
+
+static int series_launches(nd_handle *h, const void *md, cudaStream_t st, const Replica *reps)
+{
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    for (auto &c : h->classes)
+        ND_CUDA(launch_series_append(prec, reps ? reps : h->reps_d, c.work_d, (int)c.reps.size(), md, h->series,
+                                     h->series_count, h->series_cap, st));
+    ND_CUDA(launch_series_advance(h->series_count, st));
+    return ND_OK;
+}
+
+int nd_series_reset(nd_handle *h, int capacity)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (capacity < 1) return fail(ND_ERR_ARG, "capacity must be >= 1");
+    const int B = (int)h->rep_disk.size();
+    cudaFree(h->series);
+    h->series = nullptr;
+    h->series_cap = 0;
+    ND_CUDA(cudaMalloc(&h->series, sizeof(double) * 3 * (size_t)capacity * B));
+    if (!h->series_count) ND_CUDA(cudaMalloc(&h->series_count, sizeof(unsigned long long)));
+    ND_CUDA(cudaMemset(h->series_count, 0, sizeof(unsigned long long)));
+    h->series_cap = capacity;
+    return ND_OK;
+}
+
+int nd_series_sample(nd_handle *h, const void *m, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->series) return fail(ND_ERR_ARG, "nd_series_reset first");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *md = nullptr;
+    if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    return series_launches(h, md, st, nullptr);
+}
+
+int nd_series_read(nd_handle *h, double *out, long long *n_samples)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->series) return fail(ND_ERR_ARG, "nd_series_reset first");
+    unsigned long long n = 0;
+    ND_CUDA(cudaDeviceSynchronize());
+    ND_CUDA(cudaMemcpy(&n, h->series_count, sizeof(n), cudaMemcpyDeviceToHost));
+    if (n_samples) *n_samples = (long long)n;
+    const size_t kept = n < (unsigned long long)h->series_cap ? (size_t)n : (size_t)h->series_cap;
+    if (out && kept) {
+        const int B = (int)h->rep_disk.size();
+        for (int r = 0; r < B; ++r)
+            ND_CUDA(cudaMemcpy(out + (size_t)r * kept * 3, h->series + (size_t)r * h->series_cap * 3,
+                               sizeof(double) * 3 * kept, cudaMemcpyDeviceToHost));
+    }
+    return ND_OK;
+}
+
+int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_seconds, double *psd_out,
+                      double *freq_out, int *n_windows, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->series) return fail(ND_ERR_ARG, "nd_series_reset first");
+    if (component < 0 || component > 2) return fail(ND_ERR_ARG, "component must be 0, 1 or 2");
+    if (window != 64 && window != 128 && window != 256 && window != 512 && window != 1024)
+        return fail(ND_ERR_ARG, "window must be 64, 128, 256, 512 or 1024");
+    if (!(dt_sample_seconds > 0)) return fail(ND_ERR_ARG, "dt_sample_seconds must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    ND_CUDA(cudaStreamSynchronize(st));
+    unsigned long long n = 0;
+    ND_CUDA(cudaMemcpy(&n, h->series_count, sizeof(n), cudaMemcpyDeviceToHost));
+    const long long kept = n < (unsigned long long)h->series_cap ? (long long)n : (long long)h->series_cap;
+    const int nwin = (int)(kept / window), nk = window / 2 + 1;
+    if (n_windows) *n_windows = nwin;
+    if (nwin < 1) return fail(ND_ERR_ARG, "fewer recorded samples than one window");
+    const int B = (int)h->rep_disk.size();
+    if (!h->tw64.count(window)) {
+        std::vector<double> t64(2 * window);
+        for (int k = 0; k < window; ++k) {
+            t64[2 * k] = cos(2.0 * M_PI * k / window);
+            t64[2 * k + 1] = -sin(2.0 * M_PI * k / window);
+        }
+        void *p = nullptr;
+        ND_CUDA(cudaMalloc(&p, sizeof(double) * 2 * window));
+        h->tw64[window] = p;
+        ND_CUDA(cudaMemcpy(p, t64.data(), sizeof(double) * 2 * window, cudaMemcpyHostToDevice));
+    }
+    const size_t need = (size_t)B * nwin * nk + (size_t)B * nk;
+    if (need > h->psd_work_doubles) {
+        cudaFree(h->psd_work);
+        h->psd_work = nullptr;
+        h->psd_work_doubles = 0;
+        ND_CUDA(cudaMalloc(&h->psd_work, sizeof(double) * need));
+        h->psd_work_doubles = need;
+    }
+    double *pw = h->psd_work, *psd = pw + (size_t)B * nwin * nk;
+    ND_CUDA(launch_window_power(window, h->series, h->series_cap, component, nwin, B, h->tw64[window], pw, st));
+    ND_CUDA(launch_psd_reduce(pw, nwin, nk, B, dt_sample_seconds / window, psd, st));
+    if (psd_out) ND_CUDA(cudaMemcpyAsync(psd_out, psd, sizeof(double) * B * nk, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    if (freq_out)
+        for (int k = 0; k < nk; ++k) freq_out[k] = k / (window * dt_sample_seconds);
+    return ND_OK;
+}
+
 int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream)
 {
     if (int rc = check_handle(h)) return rc;
@@ -1131,7 +1243,8 @@ int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double
     if (n_steps < 1 || !(dt_seconds > 0)) return fail(ND_ERR_ARG, "n_steps >= 1 and dt > 0 required");
     if (!m || !is_device_ptr(m)) return fail(ND_ERR_ARG, "a graph needs a device state buffer");
     if (method == ND_METHOD_HEUN && (!T_kelvin || !seed)) return fail(ND_ERR_ARG, "T_kelvin and seed are required");
-    if (stats_sample && !h->stats) return fail(ND_ERR_ARG, "stats_sample needs nd_stats_reset first");
+    if ((stats_sample & ND_GRAPH_STATS) && !h->stats) return fail(ND_ERR_ARG, "statistics sample needs nd_stats_reset first");
+    if ((stats_sample & ND_GRAPH_SERIES) && !h->series) return fail(ND_ERR_ARG, "series sample needs nd_series_reset first");
     const int B = (int)h->rep_disk.size();
     const int mode = method == ND_METHOD_RK4 ? M_RK4 : M_HEUN;
     nd_graph *g = new nd_graph();
@@ -1168,7 +1281,8 @@ int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double
     if ((e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return bail(ND_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
     int rc = run_mode(h, mode, false, m, nullptr, n_steps, g->cap, g->reps);
-    if (rc == ND_OK && stats_sample) rc = stats_launches(h, m, n_steps * dt_seconds, g->cap, g->reps);
+    if (rc == ND_OK && (stats_sample & ND_GRAPH_STATS)) rc = stats_launches(h, m, n_steps * dt_seconds, g->cap, g->reps);
+    if (rc == ND_OK && (stats_sample & ND_GRAPH_SERIES)) rc = series_launches(h, m, g->cap, g->reps);
     if (rc == ND_OK && launch_advance_steps(g->reps, B, n_steps, g->cap) != cudaSuccess) rc = ND_ERR_CUDA;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->cap, &graph);

@@ -7,6 +7,7 @@ cudaError_t upload_tw_fused_f32(const double *, const double *);
 cudaError_t upload_tw_fused_f64(const double *, const double *);
 cudaError_t upload_tw_glob_f32(const double *, const double *);
 cudaError_t upload_tw_glob_f64(const double *, const double *);
+cudaError_t upload_tw_spectra(const double *, const double *);
 size_t fused_smem_f32(int P, int D, int Dpad, bool wbuf, int variant);
 size_t fused_smem_f64(int P, int D, int Dpad, bool wbuf, int variant);
 int fused_blocks_per_sm_f32(int P, int mode, size_t smem, int variant);
@@ -23,6 +24,7 @@ cudaError_t upload_twiddle_constants(const double *re, const double *im)
     if ((e = upload_tw_fused_f32(re, im)) != cudaSuccess) return e;
     if ((e = upload_tw_fused_f64(re, im)) != cudaSuccess) return e;
     if ((e = upload_tw_glob_f32(re, im)) != cudaSuccess) return e;
+    if ((e = upload_tw_spectra(re, im)) != cudaSuccess) return e;
     return upload_tw_glob_f64(re, im);
 }
 

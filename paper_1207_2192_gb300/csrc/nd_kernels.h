@@ -93,6 +93,16 @@ cudaError_t launch_advance_steps(Replica *reps, int n, long long steps, cudaStre
 cudaError_t launch_mean_m(int prec, const Replica *reps, const int *work, int nwork, const void *y,
                           double *out /*[nrep][3]*/, cudaStream_t st);
 cudaError_t launch_convert(int to_prec, const void *src, void *dst, size_t n, cudaStream_t st);
+
+// Time series of <m> and their power spectra (nd_spectra.cu).
+cudaError_t launch_series_append(int prec, const Replica *reps, const int *work, int nwork, const void *y,
+                                 double *series /*[nrep][cap][3]*/, const unsigned long long *count, int cap,
+                                 cudaStream_t st);
+cudaError_t launch_series_advance(unsigned long long *count, cudaStream_t st);
+cudaError_t launch_window_power(int W, const double *series, int cap, int comp, int nwin, int nrep,
+                                const void *twW /*length-W FP64 table*/, double *pw /*[nrep][nwin][W/2+1]*/,
+                                cudaStream_t st);
+cudaError_t launch_psd_reduce(const double *pw, int nwin, int nk, int nrep, double scale, double *psd, cudaStream_t st);
 cudaError_t launch_check_finite(int prec, const Replica *reps, const int *work, int nwork, int maxD, const void *y,
                                 unsigned *flag, cudaStream_t st);
 

@@ -58,3 +58,17 @@ def omega_from_core(xc, yc, dtau):
 def omega_thiele(kF, a, L, A, Q=1):
     """Omega_G = -kF a^2 / (4 pi L A Q) (Eq. OG)."""
     return -kF * a * a / (4.0 * math.pi * L * A * Q)
+
+
+def spectrum_peak(freq, psd, kmin=1):
+    """Frequency of the largest peak of a power spectrum (bins k >= kmin),
+    refined by a parabola through the logarithms of the peak bin and its two
+    neighbours."""
+    freq, psd = np.asarray(freq, dtype=np.float64), np.asarray(psd, dtype=np.float64)
+    k = kmin + int(np.argmax(psd[kmin:]))
+    if k <= 0 or k >= len(psd) - 1:
+        return float(freq[k])
+    a, b, c = np.log(psd[k - 1:k + 2])
+    den = a - 2 * b + c
+    d = 0.0 if den == 0 else 0.5 * (a - c) / den
+    return float(freq[k] + d * (freq[1] - freq[0]))
