@@ -72,3 +72,42 @@ def spectrum_peak(freq, psd, kmin=1):
     den = a - 2 * b + c
     d = 0.0 if den == 0 else 0.5 * (a - c) / den
     return float(freq[k] + d * (freq[1] - freq[0]))
+
+
+MU0 = 4.0e-7 * math.pi
+
+
+def geometry_sweep(Rs, Ls, a=2e-9, tol=1e-5, max_iter=60000, precision=None, stream=None):
+    """Force constant, Thiele frequency and thickness derivative of a set of
+    disks (Sec. IV's scan of f_G, k_F/L and Omega_G against L/R), all in one
+    handle: two replicas per disk, cores pinned at X = 0 and X = 2a, relaxed
+    in one batched call over every size class.
+
+    Returns one dict per disk with R, L, aspect = L/R, kF (N/m, two-point
+    Eq. Ux), kF_per_L, kF_scaled = kF / (mu0 Ms^2 L^2 / R) (the paper's fit
+    reads ~0.878), Omega (Thiele, Eq. OG, per time unit), f_G (Hz), dkF_dL
+    (envelope theorem), iters and converged."""
+    from . import Disk, Nanodisk
+    from ._binding import ND_FP32
+    disks = [Disk(R, L, a=a) for R, L in zip(Rs, Ls)]
+    h = Nanodisk(disks, [2] * len(disks), ND_FP32 if precision is None else precision)
+    X = np.zeros((h.B, 2))
+    X[1::2, 0] = 2 * a
+    m = h.empty_device()
+    h.init_vortex(m, X, stream=stream)
+    rc, U, lam, it = h.relax(m, X, tol=tol, max_iter=max_iter, stream=stream)
+    if rc not in (ND_OK, ND_ERR_NOT_CONVERGED):
+        raise RuntimeError(f"relaxation failed ({rc})")
+    E, dEdL = nd_energy(h.h, m, h.B, stream, with_dL=True)
+    out = []
+    for d, disk in enumerate(disks):
+        J = h.units[d][4]
+        t0 = h.units[d][3]
+        i0, i1 = 2 * d, 2 * d + 1
+        kF = 2.0 * (E[i1] - E[i0]) * J / (2 * a) ** 2
+        om = omega_thiele(kF, a, disk.L, disk.A)
+        out.append(dict(R=disk.R, L=disk.L, aspect=disk.L / disk.R, kF=kF, kF_per_L=kF / disk.L,
+                        kF_scaled=kF / (MU0 * disk.Ms ** 2 * disk.L ** 2 / disk.R), Omega=om,
+                        f_G=abs(om) / (2 * math.pi) / t0, dkF_dL=2.0 * (dEdL[i1] - dEdL[i0]) / (2 * a) ** 2,
+                        iters=(int(it[i0]), int(it[i1])), converged=bool(it[i0] < max_iter and it[i1] < max_iter)))
+    return out
