@@ -110,8 +110,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/nd_clocks_{os.getpid()}.csv"
+        # the raw samples go to $ND_CLOCKS_CSV if set, else to a temporary file
+        self.path = os.environ.get("ND_CLOCKS_CSV") or os.path.join(
+            os.environ.get("TMPDIR", "/tmp"), f"nd_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
