@@ -60,10 +60,14 @@ template <> __device__ __forceinline__ vec3<float> thermal_normals<float>(uint64
     const float s32 = 2.3283064365386963e-10f;
     // u = (r + 1) 2^-32 in (0, 1]: the word rounded to float, scaled exactly, then offset
     float u0 = __fmaf_rn(__uint2float_rn(r.x), s32, s32), u2 = __fmaf_rn(__uint2float_rn(r.z), s32, s32);
-    float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s3, c3;
-    sincospif(2.0f * __uint2float_rn(r.y) * s32, &s1, &c1);
-    sincospif(2.0f * __uint2float_rn(r.w) * s32, &s3, &c3);
+    // the hardware approximations (absolute error ~2^-21 on these ranges, far
+    // below the FP32 step's own rounding of sigma w); the clamp keeps
+    // -2 log u >= 0 where u rounds to just below 1
+    float ra = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f)), rb = sqrtf(fmaxf(-2.0f * __logf(u2), 0.0f));
+    const float two_pi = 6.283185307179586f;
+    float s1, c1;
+    __sincosf(two_pi * (__uint2float_rn(r.y) * s32), &s1, &c1);
+    const float c3 = __cosf(two_pi * (__uint2float_rn(r.w) * s32));
     return {ra * c1, ra * s1, rb * c3};
 }
 

@@ -52,6 +52,11 @@ template <typename T> struct V3Ptr {
     T *p;
     long long s;  // component stride
     __device__ __forceinline__ vec3<T> ld(long long i) const { return {p[i], p[s + i], p[2 * s + i]}; }
+    // bypassing L1: for data another CTA may have written during this launch
+    __device__ __forceinline__ vec3<T> ldcg(long long i) const
+    {
+        return {__ldcg(p + i), __ldcg(p + s + i), __ldcg(p + 2 * s + i)};
+    }
     __device__ __forceinline__ void st(long long i, vec3<T> v) const { p[i] = v.x; p[s + i] = v.y; p[2 * s + i] = v.z; }
 };
 
@@ -62,10 +67,12 @@ template <typename T> struct V3Ptr {
 // Returns the cell's contribution to the reduced quantity (energy mode).
 // For Heun, wbuf (when not null) keeps the predictor's normals for the
 // corrector, which then reads them instead of regenerating them.
+// ynl, accl: where y_n and the accumulator are read from (the same arrays, or
+// copies of them staged in shared memory); writes always go to yn and acc.
 template <typename T, int MODE>
 __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long long si, long long mi, vec3<T> b,
                                                 V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
-                                                unsigned long long step, V3Ptr<T> wbuf = V3Ptr<T>{nullptr, 0})
+                                                unsigned long long step, V3Ptr<T> wbuf, V3Ptr<T> ynl, V3Ptr<T> accl)
 {
     const StepParams<T> sp = step_params<T>(r);
     const T alpha = sp.alpha, dt = sp.dtau;
@@ -84,11 +91,11 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
             acc.st(si, k);
             ms.st(mi, axpy3(T(0.5) * dt, k, m));
         } else if (stage < 3) {
-            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            vec3<T> a = accl.ld(si), y = ynl.ld(si);
             acc.st(si, axpy3(T(2), k, a));
             ms.st(mi, axpy3(stage == 1 ? T(0.5) * dt : dt, k, y));
         } else {
-            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            vec3<T> a = accl.ld(si), y = ynl.ld(si);
             vec3<T> s = {a.x + k.x, a.y + k.y, a.z + k.z};
             vec3<T> yo = normalize3(axpy3(dt / T(6), s, y));
             yn.st(si, yo);
@@ -113,7 +120,7 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
             acc.st(si, d);
             ms.st(mi, normalize3(vec3<T>{m.x + d.x, m.y + d.y, m.z + d.z}));
         } else {
-            vec3<T> a = acc.ld(si), y = yn.ld(si);
+            vec3<T> a = accl.ld(si), y = ynl.ld(si);
             vec3<T> yo = normalize3(vec3<T>{y.x + T(0.5) * (a.x + d.x), y.y + T(0.5) * (a.y + d.y),
                                             y.z + T(0.5) * (a.z + d.z)});
             yn.st(si, yo);
@@ -122,6 +129,14 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
         return 0.0;
     }
     return 0.0;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long long si, long long mi, vec3<T> b,
+                                                V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
+                                                unsigned long long step, V3Ptr<T> wbuf = V3Ptr<T>{nullptr, 0})
+{
+    return epilogue_cell<T, MODE>(r, cell, si, mi, b, ms, yn, acc, out, stage, step, wbuf, yn, acc);
 }
 
 template <int MODE> struct ModeStages { static constexpr int n = 1; };
@@ -303,7 +318,7 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
         for (int cell = tid; cell < DD; cell += NT) {
             const int y = cell / D, x = cell - y * D;
             const long long si = (long long)y * Dpad + x;
-            vec3<T> v = r.mask[cell] ? yn.ld(si) : vec3<T>{T(0), T(0), T(0)};
+            vec3<T> v = r.mask[cell] ? yn.ldcg(si) : vec3<T>{T(0), T(0), T(0)};   // may come from another CTA
             ms.st(si, v);
         }
         __syncthreads();
@@ -389,6 +404,28 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
                     continue;
                 }
                 const unsigned long long step = step_base + r.step0 + (unsigned long long)(sbeg + n);
+                // Stages that read y_n and the accumulator get both copied, with
+                // 16-byte loads all in flight at once, into the FFT scratch (idle
+                // during the epilogue) instead of two dependent round trips to L2
+                // per cell.
+                V3Ptr<T> ynl = yn, accl = acc;
+                if ((MODE == M_HEUN && stage == 1) || (MODE == M_RK4 && stage > 0)) {
+                    const long long words = 3 * ms_s * (long long)sizeof(T) / 16;   // Dpad is a multiple of 4
+                    const bool fits = 2 * words * 16 <= (long long)(NGRP * Gm::SCRATCH * sizeof(cplx<T>));
+                    const bool aligned = ((reinterpret_cast<uintptr_t>(yn.p) | reinterpret_cast<uintptr_t>(acc.p)) & 15) == 0;
+                    if (fits && aligned) {
+                        int4 *dst = reinterpret_cast<int4 *>(scratch);
+                        const int4 *gy = reinterpret_cast<const int4 *>(yn.p), *ga = reinterpret_cast<const int4 *>(acc.p);
+                        for (long long i = tid; i < words; i += NT) {
+                            const int4 u = __ldcg(gy + i), v = __ldcg(ga + i);
+                            dst[i] = u;
+                            dst[words + i] = v;
+                        }
+                        __syncthreads();
+                        ynl = V3Ptr<T>{reinterpret_cast<T *>(scratch), ms_s};
+                        accl = V3Ptr<T>{reinterpret_cast<T *>(scratch) + 3 * ms_s, ms_s};
+                    }
+                }
                 for (int cell = tid; cell < DD; cell += NT) {
                     if (!r.mask[cell]) continue;
                     const int y = cell / D, x = cell - y * D;
@@ -398,7 +435,7 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
                     if (MODE == M_ENERGY)
                         esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step);
                     else
-                        epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step, wb);
+                        epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step, wb, ynl, accl);
                 }
                 __syncthreads();
             }
