@@ -532,83 +532,116 @@ __global__ void __launch_bounds__(NT)
                    scratch + gid.group * Gm::SCRATCH, tw, gid.gmask);
 }
 
-// Column pass for the large grids, one FFT group per (column, component):
-// groups 3j, 3j+1, 3j+2 of a CTA take components x, y, z of one column task,
-// so a thread holds a single column (R1 points) instead of the x and y
-// columns together, and the register budget leaves room for five CTAs per
-// SM.  The in-plane tensor couples x and y: after the forward transforms the
-// x and y groups leave their spectra in their own scratch areas, the CTA
-// syncs, and each group reads its partner's.  The packed real columns
-// (task 0) need no exchange (G_xy vanishes there).  The grid is persistent:
-// each CTA fills its twiddle table once and walks the (replica, column block)
-// tasks with a grid stride.
-template <int P, typename T> struct ColSplit {
-    static constexpr int NT = 96;                          // three groups of G = 32, six of 16, twelve of 8
-    static constexpr int CPB = NT / FFTGeom<P>::G / 3;     // column tasks per CTA
-    static constexpr int NCB = (P / 2 + CPB - 1) / CPB;
-    // resident CTAs per SM the kernel is compiled for (FP64 columns take twice the registers)
-    static constexpr int MINB = sizeof(T) == 8 ? 2 : 5;
+// Tiled column pass for the large grids.  A CTA takes a block of four
+// adjacent columns kx0..kx0+3 and one FFT group per (column, component): the
+// XY kernel the x and y components (eight groups; group 4c + j holds component
+// c of column kx0 + j, its partner for the in-plane tensor is group ^ 4), the
+// Z kernel the z component (four groups).  The block's [D][4] tiles move
+// between the spectrum and the groups' scratch areas as row-contiguous runs
+// of four complex words (one 32-byte sector per row: rows start on sectors,
+// SpecGeom::RS), so every sector the pass reads or writes is used whole.  The
+// packed real columns kx = 0, P/2 (group j = 0 of block 0) move their two
+// columns themselves.  Persistent grid over (replica, column block) tasks.
+template <int P, typename T, bool XY> struct ColTile {
+    static constexpr int G = FFTGeom<P>::G;
+    static constexpr int NCOMP = XY ? 2 : 1;
+    static constexpr int NG = 4 * NCOMP;
+    static constexpr int NT = NG * G;
+    static constexpr int NCB = P / 2 / 4;
+    // resident CTAs per SM the kernel is compiled for: 16 warps at 128
+    // registers (FP64 columns take twice the registers)
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : 512 / NT;
 };
 
-template <int P, typename T>
-__global__ void __launch_bounds__(ColSplit<P, T>::NT, ColSplit<P, T>::MINB)
-    k_g_cols_split(const Replica *__restrict__ reps, const int *__restrict__ work, int nwork,
-                   cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP)
+template <int P, typename T, bool XY>
+__global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB)
+    k_g_cols_tile(const Replica *__restrict__ reps, const int *__restrict__ work, int nwork,
+                  cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP)
 {
     using Gm = FFTGeom<P>;
-    using CS = ColSplit<P, T>;
-    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH, NT = CS::NT, CPB = CS::CPB;
-    static_assert(NT % (3 * G) == 0, "three groups per column");
+    using CT = ColTile<P, T, XY>;
+    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH, RS = SpecGeom<P>::RS, NT = CT::NT, SCR = Gm::SCRATCH;
+    static_assert(RS % 4 == 0, "rows start on 32-byte sectors");
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
     const int tid = threadIdx.x;
     load_twiddles<P>(tw, twP, tid, NT);
-    __syncthreads();
     GroupId<P> gid(tid);
-    const int j = gid.group / 3, c = gid.group - 3 * j, t = gid.t;
-    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
-    const cplx<T> *other = scratch + (gid.group + (c == 0 ? 1 : -1)) * Gm::SCRATCH;   // used by c < 2 only
-    for (int task = blockIdx.x; task < nwork * CS::NCB; task += gridDim.x) {
-        const int wi = task / CS::NCB, q = (task - wi * CS::NCB) * CPB + j;
+    const int g = gid.group, j = g & 3, c = XY ? (g >> 2) : 2, t = gid.t;
+    cplx<T> *scr = scratch + g * SCR;
+    const cplx<T> *other = scratch + (g ^ 4) * SCR;   // XY only
+    for (int task = blockIdx.x; task < nwork * CT::NCB; task += gridDim.x) {
+        const int wi = task / CT::NCB, cb = task - wi * CT::NCB, kx0 = 4 * cb;
         const Replica &r = reps[work[wi]];
         const int D = r.D;
-        const bool active = q < P / 2, packed = (q == 0);
-        const int kx = (active && q > 0) ? q : 1;   // idle groups still transform; keep their table reads in range
-        cplx<T> *col = specbase + r.spec_off + c * (long long)D * SpecGeom<P>::RS;
+        const long long cs = (long long)D * RS;
+        cplx<T> *spec = specbase + r.spec_off;
         const T *Ghat = reinterpret_cast<const T *>(r.Ghat);
+        const bool packed = (cb == 0 && j == 0);
+        const int kx = packed ? 1 : kx0 + j;   // (the packed group reads no kx column of the table)
+        __syncthreads();   // twiddles filled / the previous task's tiles stored
+        // tile load: element e -> column jj = e & 3, row y, component index ci
+        const int cbase = XY ? 0 : 2;
+        for (int e = tid; e < CT::NCOMP * D * 4; e += NT) {
+            const int jj = e & 3, rest = e >> 2, ci = rest / D, y = rest - ci * D;
+            if (cb == 0 && jj == 0) continue;
+            scratch[(4 * ci + jj) * SCR + y] = spec[(cbase + ci) * cs + (long long)y * RS + kx0 + jj];
+        }
+        __syncthreads();
         cplx<T> v[R1];
         if (packed) {
-            packed_col_fwd<P, T>(v, c, active, D, col, Ghat, t, gid.lane, scr, tw, gid.gmask);
+            packed_col_fwd<P, T>(v, c, true, D, spec + c * cs, Ghat, t, gid.lane, scr, tw, gid.gmask);
         } else {
-            col_load<P>(v, col + kx, D, t, active);
+#pragma unroll
+            for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+            for (int o = 0; o < R1 / 2; ++o) {   // rows >= D (and so >= P/2) are zero padding
+                const int y = t + G * o;
+                if (y < D) v[o] = scr[y];
+            }
+            __syncwarp(gid.gmask);
             fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gid.gmask);
-            if (c < 2) {
+            if (XY) {
 #pragma unroll
                 for (int o = 0; o < R1; ++o) scr[o * G + t] = v[o];
             }
         }
-        __syncthreads();
+        if (XY) __syncthreads();
         if (!packed) {
-            if (c < 2) {
+            if (XY) {
 #pragma unroll
                 for (int o = 0; o < R1; ++o) {
                     const int ky = t + G * o;
                     const bool up = ky <= P / 2;
                     const int kyr = up ? ky : P - ky;
-                    GhatVal<T> g = load_ghat<T>(Ghat, kx * KH + kyr);
-                    const T gxy = up ? g.xy : -g.xy;     // G_xy is odd in ky
+                    GhatVal<T> gv = load_ghat<T>(Ghat, kx * KH + kyr);
+                    const T gxy = up ? gv.xy : -gv.xy;   // G_xy is odd in ky
                     const cplx<T> w = other[o * G + t];
-                    v[o] = c == 0 ? tensor_row(g.xx, v[o], gxy, w) : tensor_row(gxy, w, g.yy, v[o]);
+                    v[o] = c == 0 ? tensor_row(gv.xx, v[o], gxy, w) : tensor_row(gxy, w, gv.yy, v[o]);
                 }
             } else {
                 col_multiply_z<P>(v, Ghat, kx, t);
             }
         }
-        __syncthreads();   // the partner's spectrum is read before the scratch is reused
+        if (XY) __syncthreads();   // the partner's spectrum is read before the scratch is reused
         fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gid.gmask);
-        if (packed) packed_col_store<P, T>(v, active, D, col, t);
-        else col_store<P>(v, col + kx, D, t, active);
+        __syncwarp(gid.gmask);
+        if (packed) {
+            packed_col_store<P, T>(v, true, D, spec + c * cs, t);
+        } else {
+#pragma unroll
+            for (int o = 0; o < R1 / 2; ++o) {
+                const int y = t + G * o;
+                if (y < D) scr[y] = v[o];
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < CT::NCOMP * D * 4; e += NT) {
+            const int jj = e & 3, rest = e >> 2, ci = rest / D, y = rest - ci * D;
+            if (cb == 0 && jj == 0) continue;
+            spec[(cbase + ci) * cs + (long long)y * RS + kx0 + jj] = scratch[(4 * ci + jj) * SCR + y];
+        }
     }
 }
 
@@ -800,8 +833,9 @@ inline int fused_nt(int P, int variant)
     }
 }
 template <int P> struct GlobNT { static constexpr int v = 256; };
-// The split column pass runs from P = 256 up.
-template <int P> struct GlobSplit { static constexpr bool v = P >= 256; };
+// The tiled column pass runs from P = 256 up (rows of the global spectrum
+// start on 32-byte sectors there).
+template <int P> struct GlobTiled { static constexpr bool v = P >= 256; };
 
 template <int P, typename T, int NT>
 constexpr size_t glob_smem_bytes()
@@ -925,11 +959,15 @@ static void glob_field_passes(const LaunchArgs &a, int maxD)
     dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork), gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
     const size_t sm = glob_smem_bytes<P, T, NT>();
     k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 0);
-    if constexpr (GlobSplit<P>::v) {
-        using CS = ColSplit<P, T>;
-        const int ntask = a.nwork * CS::NCB;
-        const int grid = ntask < a.n_sm * CS::MINB ? ntask : a.n_sm * CS::MINB;
-        k_g_cols_split<P, T><<<grid, CS::NT, glob_smem_bytes<P, T, CS::NT>(), a.stream>>>(
+    if constexpr (GlobTiled<P>::v) {
+        using CX = ColTile<P, T, true>;
+        using CZ = ColTile<P, T, false>;
+        const int ntask = a.nwork * CX::NCB;
+        const int gx = ntask < a.n_sm * CX::MINB ? ntask : a.n_sm * CX::MINB;
+        const int gz = ntask < a.n_sm * CZ::MINB ? ntask : a.n_sm * CZ::MINB;
+        k_g_cols_tile<P, T, true><<<gx, CX::NT, glob_smem_bytes<P, T, CX::NT>(), a.stream>>>(
+            a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+        k_g_cols_tile<P, T, false><<<gz, CZ::NT, glob_smem_bytes<P, T, CZ::NT>(), a.stream>>>(
             a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
     } else {
         k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
@@ -960,10 +998,13 @@ static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
     const int sm = (int)glob_smem_bytes<P, T, NT>();
     cudaError_t e0 = cudaFuncSetAttribute(k_g_rows<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e0 == cudaSuccess) e0 = cudaFuncSetAttribute(k_g_cols<P, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if constexpr (GlobSplit<P>::v) {
+    if constexpr (GlobTiled<P>::v) {
         if (e0 == cudaSuccess)
-            e0 = cudaFuncSetAttribute(k_g_cols_split<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)glob_smem_bytes<P, T, ColSplit<P, T>::NT>());
+            e0 = cudaFuncSetAttribute(k_g_cols_tile<P, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)glob_smem_bytes<P, T, ColTile<P, T, true>::NT>());
+        if (e0 == cudaSuccess)
+            e0 = cudaFuncSetAttribute(k_g_cols_tile<P, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)glob_smem_bytes<P, T, ColTile<P, T, false>::NT>());
     }
     if (e0 != cudaSuccess) return e0;
 
