@@ -516,7 +516,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
         return cuda_fail(e, "cudaMalloc");
     for (int d = 0; d < n_disks; ++d) {
         DiskInfo &di = h->disks[d];
-        const size_t kh = (size_t)(di.P / 2 + 1) * (di.P / 2 + 1) * 4;
+        const size_t kh = ghat_table_entries(di.P);
         if ((e = cudaMalloc(&di.mask_d, di.mask.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice);
         if ((e = cudaMalloc(&di.ghat64, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");

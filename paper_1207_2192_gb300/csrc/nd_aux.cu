@@ -89,7 +89,8 @@ __global__ void k_ghat_pass1(int P, int D, const double *Gq, const double *cs, d
     }
 }
 
-// Pass 2 over dy and final assembly into [kx][ky][4]:
+// Pass 2 over dy and final assembly into [kx][ky][4], followed by the same
+// values component-major, [4][kx][ky]:
 //   Ghat_c = s_c sum_dy w(dy) T1[c][dy][kx] f_c(2 pi ky dy / P), s_xy = -1,
 //   diagonal: (c Ghat + 2 cos(2 pi kx/P) + 2 cos(2 pi ky/P)) / P^2 (exchange folded in),
 //   xy:       c Ghat_xy / P^2.
@@ -114,6 +115,9 @@ __global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const 
         for (int c = 0; c < 4; ++c) {
             G64[(size_t)i * 4 + c] = o[c];
             if (G32) G32[(size_t)i * 4 + c] = (float)o[c];
+            // the same values component-major after the interleaved block
+            G64[(size_t)(4 + c) * n + i] = o[c];
+            if (G32) G32[(size_t)(4 + c) * n + i] = (float)o[c];
         }
     }
 }

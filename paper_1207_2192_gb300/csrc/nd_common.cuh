@@ -93,7 +93,8 @@ struct Replica {
     int flags;                   // bit 0: thermal noise on
     long long state_off;         // element offset of this replica's [3][D][Dpad] block
     long long spec_off;          // complex-element offset of its [3][D][RS] spectrum (global path)
-    const void *Ghat;            // [P/2+1 (kx)][P/2+1 (ky)][4] spectral kernel, incl. exchange and 1/P^2
+    const void *Ghat;            // [P/2+1 (kx)][P/2+1 (ky)][4] spectral kernel, incl. exchange and 1/P^2,
+                                 // then the same values as [4][P/2+1][P/2+1]
     const unsigned char *mask;   // [D][D]
     double chext[3];             // (a^2/lambda^2) h_ext
     double alpha, dtau, sigma;   // damping, dimensionless step, noise amplitude

@@ -581,12 +581,15 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
         const bool packed = (cb == 0 && j == 0);
         const int kx = packed ? 1 : kx0 + j;   // (the packed group reads no kx column of the table)
         __syncthreads();   // twiddles filled / the previous task's tiles stored
-        // tile load: element e -> column jj = e & 3, row y, component index ci
-        const int cbase = XY ? 0 : 2;
-        for (int e = tid; e < CT::NCOMP * D * 4; e += NT) {
-            const int jj = e & 3, rest = e >> 2, ci = rest / D, y = rest - ci * D;
-            if (cb == 0 && jj == 0) continue;
-            scratch[(4 * ci + jj) * SCR + y] = spec[(cbase + ci) * cs + (long long)y * RS + kx0 + jj];
+        // tile load: thread -> column jj = tid & 3 of the block, rows tid/4 + k NT/4
+        const int cbase = XY ? 0 : 2, jj = tid & 3;
+        if (!(cb == 0 && jj == 0)) {
+#pragma unroll
+            for (int ci = 0; ci < CT::NCOMP; ++ci) {
+                const cplx<T> *src = spec + (cbase + ci) * cs + kx0 + jj;
+                cplx<T> *dst = scratch + (4 * ci + jj) * SCR;
+                for (int y = tid >> 2; y < D; y += NT / 4) dst[y] = src[(long long)y * RS];
+            }
         }
         __syncthreads();
         cplx<T> v[R1];
@@ -609,19 +612,30 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
         }
         if (XY) __syncthreads();
         if (!packed) {
+            // the component-major copy of the table: each group reads only the
+            // entries it uses (4 or 8 bytes per point instead of 16)
+            constexpr int KK = KH * KH;
+            const T *Gs = Ghat + 4 * KK + kx * KH;
             if (XY) {
+                const T *gd = Gs + c * KK, *go = Gs + 2 * KK;   // diagonal entry (xx or yy), xy
 #pragma unroll
                 for (int o = 0; o < R1; ++o) {
                     const int ky = t + G * o;
                     const bool up = ky <= P / 2;
                     const int kyr = up ? ky : P - ky;
-                    GhatVal<T> gv = load_ghat<T>(Ghat, kx * KH + kyr);
-                    const T gxy = up ? gv.xy : -gv.xy;   // G_xy is odd in ky
+                    const T gdiag = __ldg(gd + kyr), gxy0 = __ldg(go + kyr);
+                    const T gxy = up ? gxy0 : -gxy0;   // G_xy is odd in ky
                     const cplx<T> w = other[o * G + t];
-                    v[o] = c == 0 ? tensor_row(gv.xx, v[o], gxy, w) : tensor_row(gxy, w, gv.yy, v[o]);
+                    v[o] = c == 0 ? tensor_row(gdiag, v[o], gxy, w) : tensor_row(gxy, w, gdiag, v[o]);
                 }
             } else {
-                col_multiply_z<P>(v, Ghat, kx, t);
+                const T *gz = Gs + 3 * KK;
+#pragma unroll
+                for (int o = 0; o < R1; ++o) {
+                    const int ky = t + G * o;
+                    const int kyr = ky <= P / 2 ? ky : P - ky;
+                    v[o] = cscale(v[o], __ldg(gz + kyr));
+                }
             }
         }
         if (XY) __syncthreads();   // the partner's spectrum is read before the scratch is reused
@@ -637,10 +651,13 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
             }
         }
         __syncthreads();
-        for (int e = tid; e < CT::NCOMP * D * 4; e += NT) {
-            const int jj = e & 3, rest = e >> 2, ci = rest / D, y = rest - ci * D;
-            if (cb == 0 && jj == 0) continue;
-            spec[(cbase + ci) * cs + (long long)y * RS + kx0 + jj] = scratch[(4 * ci + jj) * SCR + y];
+        if (!(cb == 0 && jj == 0)) {
+#pragma unroll
+            for (int ci = 0; ci < CT::NCOMP; ++ci) {
+                cplx<T> *dst = spec + (cbase + ci) * cs + kx0 + jj;
+                const cplx<T> *src = scratch + (4 * ci + jj) * SCR;
+                for (int y = tid >> 2; y < D; y += NT / 4) dst[(long long)y * RS] = src[y];
+            }
         }
     }
 }

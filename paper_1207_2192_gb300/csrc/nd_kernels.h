@@ -69,7 +69,10 @@ size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] 
 // Spectral kernel build (Section II.B tensor, cell self terms, exchange folded in).
 // Gq: optional device table [4][D][D] of a^2 G at displacements (dx, dy) >= 0 (comps xx, yy, xy, zz,
 // self terms at the origin); when null it is computed from the paper's closed forms.
-// Output: Ghat64 [P/2+1][P/2+1][4] doubles and, if Ghat32 != null, a float copy.
+// Output: Ghat64 [P/2+1][P/2+1][4] doubles followed by the same values
+// component-major, [4][P/2+1][P/2+1] (ghat_table_entries(P) doubles in all),
+// and, if Ghat32 != null, a float copy of the same layout.
+inline size_t ghat_table_entries(int P) { return (size_t)(P / 2 + 1) * (P / 2 + 1) * 8; }
 cudaError_t build_ghat(int P, int D, double L_over_a, double Nx, double Nz, double c, const double *Gq_dev,
                        double *Ghat64, float *Ghat32, double *work, cudaStream_t st);
 size_t build_ghat_work_doubles(int P, int D);

@@ -36,7 +36,7 @@ namespace {
 constexpr size_t kAccFloats = ND_NOALLOC_MAX_STATE_FLOATS;   // stage accumulator capacity
 constexpr int kMaxReplicas = ND_NOALLOC_MAX_REPLICAS;
 constexpr int kMaxP = 128, kMaxD = 64, kKH = kMaxP / 2 + 1;
-constexpr size_t kGhatEntries = (size_t)kKH * kKH * 4;
+constexpr size_t kGhatEntries = (size_t)kKH * kKH * 8;   // interleaved and component-major copies
 
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 // layout of the static array (byte offsets)
