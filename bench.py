@@ -10,14 +10,16 @@ by the per-replica statistics sample (vortex core estimator, FP64 moments and
 uint64 histograms of r and V, all on the device).  A cell-update is one time step of one disk cell of one replica.
 
 Other workloads: "large_disk" (8 replicas of R = 500 nm, L = 20 nm, FFT grid
-1024 x 1024, Heun at 300 K) and "plain" (the batched workload's disk as a
-single replica).
+1024 x 1024, Heun at 300 K: the HBM-bound configuration) and "plain" (the
+batched workload's disk as a single replica).
 
 The JSON line also carries: the plain single-replica number (batched vs
 plain), the roofline of the dominant kernel, the end-to-end number through the
 C ABI with host buffers, SM clocks sampled during the timed region, and the
-FP64 CPU oracle timed on the host cores.  With --impl reference the oracle
-alone is timed as the reference arm.
+FP64 CPU oracle timed on the host cores.  A default run (batched_heun) also
+times the large-disk workload the same way and nests its record, with its own
+HBM roofline, e2e, clocks and oracle sample, under "large_disk".  With --impl
+reference the oracle alone is timed as the reference arm.
 """
 from __future__ import annotations
 
@@ -54,9 +56,15 @@ def fft_flops_per_eval(P, C):
     return 6 * 2.5 * P * P * math.log2(P * P) + 14 * P * (P // 2 + 1) + 60 * C
 
 
-def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152, lanes=128):
-    """FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock."""
+def fp32_alu_peak_tflops(sms, sm_mhz=2070.0, lanes=128):
+    """FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock (the device's SM
+    count, 128 FP32 lanes per SM, the maximum SM clock)."""
     return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_sms(device=0):
+    import torch
+    return torch.cuda.get_device_properties(device).multi_processor_count
 
 
 # The sources that make up each workload's dominant kernel: its translation
@@ -233,32 +241,39 @@ def global_path_bytes_per_step(wl):
     return 2 * per_eval * CHUNK
 
 
-def run_ours(args, rank, world, local_rank):
+def kernel_name(wl):
+    """Name of the kernel that steps the workload's size class under the plan
+    the handle uses (fused on-chip kernel with its thread count, or the global
+    path)."""
+    info = wl.nd.nd_plan_info(wl.h.h, 0)
+    if info and info["threads_heun"] > 0:
+        return f"k_fused<{wl.P},float,HEUN,{info['threads_heun']}>"
+    return "global-path Heun step (k_g_rows, k_g_cols_tile x/y and z, k_g_epi)"
+
+
+def measure(name, steps, warmup, world, local_rank, dist, flush):
+    """Time one workload: graph replays in the device-timed region (L2 flushed
+    before each), nd_step_heun alone for the roofline, and nd_step_heun on
+    pinned host buffers end to end.  Returns (record or None off rank 0, wl)."""
     import torch
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    wl = Workload(args.workload, local_rank)
-    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    wl = Workload(name, local_rank)
+    for _ in range(warmup):
         wl.run_step()
     wl.make_graph()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         wl.nd.nd_graph_launch(wl.graph, wl.stream)
         wl.step += CHUNK
     torch.cuda.synchronize()
 
     # ---- device-timed region: graph replays (CHUNK Heun steps + statistics
     # sample), inputs resident in HBM, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
-        for i in range(args.steps):
+        for i in range(steps):
             l2_flush(torch, flush)
             ev[i][0].record()
             wl.nd.nd_graph_launch(wl.graph, wl.stream)
@@ -281,8 +296,7 @@ def run_ours(args, rank, world, local_rank):
         wl.step += CHUNK
     torch.cuda.synchronize()
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    cu_rank = wl.cell_updates_per_step() * args.steps
-    cu = cu_rank * world
+    cu_rank = wl.cell_updates_per_step() * steps
     value = whole_job_rate(cu_rank, world, total_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
@@ -293,54 +307,84 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for i in range(args.steps):
+    for i in range(steps):
         wl.nd.nd_step_heun(wl.h.h, host.data_ptr(), CHUNK, DT, wl.T, wl.seeds, wl.step, None)
         wl.step += CHUNK
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = whole_job_rate(cu_rank, world, e2e_s)
+    if os.environ.get("RANK", "0") != "0":
+        return None, wl
 
+    peaks = measured_peaks()
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    timing = "CUDA events around nd_step_heun on the bench stream, 5 launches, L2 flushed"
+    if wl.P <= 128:
+        flop_cu = 2 * fft_flops_per_eval(wl.P, wl.C) / wl.C          # per cell-update (Heun = 2 evaluations)
+        achieved = flop_cu * wl.cell_updates_per_step() / kern_avg_s / 1e12
+        sms = device_sms(local_rank)
+        peak = fp32_alu_peak_tflops(sms)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(name), "kernel": kernel_name(wl), "flops_per_cell_update": flop_cu,
+                "units_per_launch": wl.cell_updates_per_step(),
+                "peak_note": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x 2070 MHz, derived from unit counts "
+                             "(MEASURED_PEAKS.json has no FP32 entry)",
+                "timing": timing}
+    else:
+        nbytes_step = global_path_bytes_per_step(wl)
+        achieved = nbytes_step / kern_avg_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(name), "kernel": kernel_name(wl),
+                "bytes_per_cell_update": nbytes_step / wl.cell_updates_per_step(),
+                "units_per_launch": wl.cell_updates_per_step(),
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" +
+                             (" -- fallback value" if peaks.get("fallback") else ""),
+                "timing": timing}
+    rec = {
+        "value": value, "unit": "cell-updates/s", "steps": steps, "ms_per_step": total_ms / steps,
+        "config": {"workload": name, "replicas_per_gpu": wl.B, "R_nm": wl.disk.R * 1e9,
+                   "L_nm": wl.disk.L * 1e9, "a_nm": wl.disk.a * 1e9, "D": wl.D, "cells": wl.C, "P": wl.P,
+                   "T_K": T_K, "alpha": ALPHA, "dt_fs": DT * 1e15, "heun_steps_per_bench_step": CHUNK,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "launch": "one CUDA graph per bench step (nd_graph_create)"},
+        "roofline": roof,
+        "kernel_ms_per_step": statistics.mean(kern_ms),
+        "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    return rec, wl
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rec, wl = measure(args.workload, args.steps, args.warmup, world, local_rank, dist, flush)
+    large = None
+    if args.workload == "batched_heun" and args.large_steps > 0:
+        # the HBM-bound configuration, timed the same way, nested in the line
+        large, _ = measure("large_disk", args.large_steps, args.warmup, world, local_rank, dist, flush)
     result = None
     if rank == 0:
         peaks = measured_peaks()
-        clocks = clk.summary()
-        flop_cu = 2 * fft_flops_per_eval(wl.P, wl.C) / wl.C          # per cell-update (Heun = 2 evaluations)
-        kern_avg_s = statistics.mean(kern_ms) / 1e3
-        if wl.P <= 128:
-            achieved = flop_cu * wl.cell_updates_per_step() / kern_avg_s / 1e12
-            peak = fp32_alu_peak_tflops()
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": profiled_traffic(args.workload), "kernel": "k_fused<128,float,HEUN,512>", "flops_per_cell_update": flop_cu,
-                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (MEASURED_PEAKS.json has no FP32 entry)",
-                    "timing": "CUDA events around nd_step_heun on the bench stream, 5 launches, L2 flushed"}
-        else:
-            nbytes_step = global_path_bytes_per_step(wl)
-            achieved = nbytes_step / kern_avg_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": profiled_traffic(args.workload),
-                    "kernel": "global-path Heun step (k_g_rows, k_g_cols_split, k_g_epi)",
-                    "bytes_per_cell_update": nbytes_step / wl.cell_updates_per_step(),
-                    "peak_note": "measured copy bandwidth, MEASURED_PEAKS.json",
-                    "timing": "CUDA events around nd_step_heun on the bench stream, 5 launches, L2 flushed"}
         result = {
-            "metric": "LLG cell-updates/sec", "value": value, "unit": "cell-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "metric": "LLG cell-updates/sec", "value": rec["value"], "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (analytic centred vortex, Philox thermal noise)",
-            "config": {"workload": args.workload, "replicas_per_gpu": wl.B, "R_nm": wl.disk.R * 1e9,
-                       "L_nm": wl.disk.L * 1e9, "a_nm": wl.disk.a * 1e9, "D": wl.D, "cells": wl.C, "P": wl.P,
-                       "T_K": T_K, "alpha": ALPHA, "dt_fs": DT * 1e15, "heun_steps_per_bench_step": CHUNK,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "launch": "one CUDA graph per bench step (nd_graph_create)"},
-            "roofline": roof,
-            "kernel_ms_per_step": statistics.mean(kern_ms),
-            "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "config": rec["config"], "roofline": rec["roofline"], "kernel_ms_per_step": rec["kernel_ms_per_step"],
+            "e2e": rec["e2e"], "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
         }
         if "hbm_gbs" in peaks:
             result["hbm_peak_gbs"] = peaks["hbm_gbs"]
+        if large is not None:
+            result["large_disk"] = large
     if dist:
         dist.destroy_process_group()
     return result, wl
@@ -430,6 +474,8 @@ def main():
     ap.add_argument("--workload", default="batched_heun", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=150,
+                    help="bench steps of the nested large-disk record (0: skip it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -450,6 +496,10 @@ def main():
             rate, sample, cores = oracle_rate(args.workload)
             result["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                                       "sample": sample}
+            if "large_disk" in result:
+                rate, sample, cores = oracle_rate("large_disk", budget_s=8.0)
+                result["large_disk"]["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores,
+                                                        "kind": "oracle", "sample": sample}
         print(json.dumps(result), flush=True)
 
 

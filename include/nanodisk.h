@@ -332,7 +332,7 @@ void nd_graph_destroy(nd_graph *g);
  * a message: padded grid P <= 128 (disk diameter up to 64 cells, and the
  * on-chip kernel must fit, about 60 cells), n_replicas <= ND_NOALLOC_MAX_REPLICAS,
  * n_replicas * 3 * D * Dpad <= ND_NOALLOC_MAX_STATE_FLOATS, and m must be a
- * device pointer.
+ * device pointer on the current device (a buffer of another GPU is rejected).
  *
  * The first call on a device resolves the array's address on that device and
  * loads the FFT constants; make that first call before any stream capture.

@@ -67,6 +67,10 @@ def lib():
                 "ndo_omega_G": (_D, [_D, _D, _D, _D, _I]),
                 "ndo_kF_from_energies": (_D, [_D, _D, _D]),
                 "ndo_p_r": (_D, [_D, _D, _D]),
+                "ndo_gyro_mass": (_D, [_D, _D]),
+                "ndo_f_V": (_D, [_D, _D, _D]),
+                "ndo_omega_from_track": (_D, [_P, _P, _I, _D]),
+                "ndo_power_spectrum": (_I, [_P, ctypes.c_long, _I, _D, _P]),
                 "ndo_grid_side": (_I, [_D, _D]),
                 "ndo_mask": (_I, [_D, _D, _I, _P]),
                 "ndo_green": (None, [_D, _D, _D, _P]),
@@ -79,6 +83,7 @@ def lib():
                 "ndo_model_params": (None, [_P, _P]),
                 "ndo_model_mask": (None, [_P, _P]),
                 "ndo_model_set_alpha": (None, [_P, _D]),
+                "ndo_model_set_green": (None, [_P, _P]),
                 "ndo_demag": (None, [_P, _P, _P]),
                 "ndo_field": (None, [_P, _P, _P]),
                 "ndo_field_parts": (None, [_P, _P, _P, _P]),
@@ -147,6 +152,30 @@ def p_r(r, kF, kT):
     return lib().ndo_p_r(r, kF, kT)
 
 
+def gyro_mass(G, kF):
+    return lib().ndo_gyro_mass(G, kF)
+
+
+def f_V(V, mG, kT):
+    return lib().ndo_f_V(V, mG, kT)
+
+
+def omega_from_track(xc, yc, dtau):
+    """Slope of the continuous polar angle of a core track against tau."""
+    xc = np.ascontiguousarray(xc, dtype=np.float64)
+    yc = np.ascontiguousarray(yc, dtype=np.float64)
+    assert xc.shape == yc.shape and xc.ndim == 1
+    return lib().ndo_omega_from_track(_ptr(xc), _ptr(yc), len(xc), dtau)
+
+
+def power_spectrum(x, window, dt):
+    """Averaged one-sided periodogram of a series; returns (psd, n_windows)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    psd = np.zeros(window // 2 + 1)
+    nw = lib().ndo_power_spectrum(_ptr(x), len(x), window, dt, _ptr(psd))
+    return psd, nw
+
+
 def green(x, y, L):
     g = np.zeros(4)
     lib().ndo_green(x, y, L, _ptr(g))
@@ -208,6 +237,26 @@ class Model:
     def set_alpha(self, alpha):
         self.alpha = alpha
         lib().ndo_model_set_alpha(self._buf, alpha)
+
+    def set_green(self, Gq):
+        """Replace the Green's table by a quarter table [4][D][D] of a^2 G at
+        displacements (dx, dy) >= 0 (components xx, yy, xy, zz; self terms at
+        the origin), extended to negative displacements by symmetry."""
+        Gq = np.ascontiguousarray(Gq, dtype=np.float64)
+        assert Gq.shape == (4, self.D, self.D), Gq.shape
+        lib().ndo_model_set_green(self._buf, _ptr(Gq))
+
+    def quarter_table(self):
+        """The closed-form quarter table of Sec. II.B for this geometry, built
+        from the oracle's Green's function and self factors."""
+        q = np.zeros((4, self.D, self.D))
+        for dy in range(self.D):
+            for dx in range(self.D):
+                if dx == 0 and dy == 0:
+                    q[:, 0, 0] = (-self.Nx, -self.Nx, 0.0, -self.Nz)
+                else:
+                    q[:, dy, dx] = green(dx * self.a, dy * self.a, self.L) * self.a ** 2
+        return q
 
     def _state(self, m):
         m = np.ascontiguousarray(m, dtype=np.float64)

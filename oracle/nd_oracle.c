@@ -91,6 +91,81 @@ double ndo_kF_from_energies(double U0, double Ux, double x) { return 2.0 * (Ux -
 /* Radial Boltzmann density p(r) = beta kF r exp(-beta kF r^2 / 2) (Eq. pr). */
 double ndo_p_r(double r, double kF, double kT) { double b = 1.0 / kT; return b * kF * r * exp(-0.5 * b * kF * r * r); }
 
+/* Gyrotropic effective mass m_G = G^2 / k_F (Sec. VI), G the gyrovector (kg/s)
+ * and k_F the force constant (N/m); kilograms. */
+double ndo_gyro_mass(double G, double kF) { return G * G / kF; }
+
+/* Boltzmann density of the vortex rotational speed (Sec. VI):
+ *   f(V) = beta m_G V exp(-beta m_G V^2 / 2),  beta = 1/kT,
+ * the image of p(r) under V = |omega_G| r. */
+double ndo_f_V(double V, double mG, double kT)
+{
+    double b = 1.0 / kT;
+    return b * mG * V * exp(-0.5 * b * mG * V * V);
+}
+
+/* Angular frequency of gyrotropic motion from a sampled core track (the
+ * dynamic side of Eq. OG): the polar angle theta_k = atan2(y_k, x_k) of each
+ * sample, made continuous by adding the multiple of 2 pi that keeps every step
+ * theta_k - theta_{k-1} within (-pi, pi], then the least-squares slope of
+ * theta against tau_k = k dtau.  Returns the slope (radians per time unit;
+ * negative for clockwise motion). */
+double ndo_omega_from_track(const double *xc, const double *yc, int n, double dtau)
+{
+    if (n < 2) return 0.0;
+    double *th = (double *)malloc(sizeof(double) * n);
+    th[0] = atan2(yc[0], xc[0]);
+    for (int k = 1; k < n; ++k) {
+        double a = atan2(yc[k], xc[k]), d = a - th[k - 1];
+        d -= 2.0 * M_PI * floor((d + M_PI) / (2.0 * M_PI));   /* into [-pi, pi) */
+        th[k] = th[k - 1] + d;
+    }
+    double st = 0.0, sth = 0.0;
+    for (int k = 0; k < n; ++k) { st += k * dtau; sth += th[k]; }
+    double tm = st / n, thm = sth / n, num = 0.0, den = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double dt_ = k * dtau - tm;
+        num += dt_ * (th[k] - thm);
+        den += dt_ * dt_;
+    }
+    free(th);
+    return num / den;
+}
+
+/* Averaged one-sided power spectrum of a sampled series (Sec. V, the thermal
+ * power spectra of <m_x>): the series x[0..n) is cut into n_w = n / W
+ * consecutive windows of W samples; each window's mean is removed; its DFT
+ * X_k = sum_t x_t exp(-2 pi i k t / W) is summed directly; and
+ *   psd[k] = c_k (dt / W) < |X_k|^2 >_windows,  k = 0..W/2,
+ * with c_k = 2 except c_0 = c_{W/2} = 1.  Returns n_w (0 if n < W, psd
+ * untouched). */
+int ndo_power_spectrum(const double *x, long n, int W, double dt, double *psd)
+{
+    int nw = (int)(n / W);
+    if (nw < 1 || W < 2) return 0;
+    for (int k = 0; k <= W / 2; ++k) psd[k] = 0.0;
+    for (int w = 0; w < nw; ++w) {
+        const double *xs = x + (size_t)w * W;
+        double mean = 0.0;
+        for (int t = 0; t < W; ++t) mean += xs[t];
+        mean /= W;
+        for (int k = 0; k <= W / 2; ++k) {
+            double re = 0.0, im = 0.0;
+            for (int t = 0; t < W; ++t) {
+                double ang = -2.0 * M_PI * (double)(((long)k * t) % W) / W;
+                re += (xs[t] - mean) * cos(ang);
+                im += (xs[t] - mean) * sin(ang);
+            }
+            psd[k] += re * re + im * im;
+        }
+    }
+    for (int k = 0; k <= W / 2; ++k) {
+        double c = (k == 0 || 2 * k == W) ? 1.0 : 2.0;
+        psd[k] *= c * dt / W / nw;
+    }
+    return nw;
+}
+
 /* ------------------------------------------------------------- geometry */
 
 int ndo_grid_side(double R, double a) { return (int)floor(2.0 * R / a + 0.5); }
@@ -170,6 +245,28 @@ int ndo_model_init(const ndo_disk *d, ndo_model *m)
             for (int k = 0; k < 4; ++k) m->Gt[(size_t)k * W * W + o] = g[k];
         }
     return 0;
+}
+
+/* Replace the model's table by a user table Gq of a^2 G at displacements
+ * (dx, dy) >= 0 cells, laid out [4][D][D] (index [k][dy][dx], components xx,
+ * yy, xy, zz, the self terms at dx = dy = 0), extended to negative
+ * displacements by the symmetry of the Sec. II.B tensor: xx, yy and zz even
+ * in dx and in dy, xy odd in each. */
+void ndo_model_set_green(ndo_model *m, const double *Gq)
+{
+    const int D = m->D, W = 2 * D - 1;
+    for (int dy = -(D - 1); dy <= D - 1; ++dy)
+        for (int dx = -(D - 1); dx <= D - 1; ++dx) {
+            int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+            /* sign(dx) sign(dy): an odd function of dx vanishes at dx = 0 */
+            double sgn = (dx > 0) - (dx < 0);
+            sgn *= (dy > 0) - (dy < 0);
+            size_t q = (size_t)ay * D + ax, o = (size_t)(dy + D - 1) * W + (dx + D - 1);
+            for (int k = 0; k < 4; ++k) {
+                double v = Gq[(size_t)k * D * D + q];
+                m->Gt[(size_t)k * W * W + o] = (k == 2) ? sgn * v : v;
+            }
+        }
 }
 
 void ndo_model_free(ndo_model *m)

@@ -114,16 +114,21 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
                                     std::to_string(kAccFloats));
     for (int r = 0; r < n_replicas; ++r)
         if (!(T_kelvin[r] >= 0)) return fail(ND_ERR_ARG, "nd_step_heun_noalloc: temperatures must be >= 0");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(ND_ERR_CUDA, "nd_step_heun_noalloc: no usable current device");
     {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, m) != cudaSuccess || !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
             cudaGetLastError();
             return fail(ND_ERR_ARG, "nd_step_heun_noalloc: m must be a device pointer (host buffers would need staging memory)");
         }
+        // the kernel runs on the current device: a buffer of another GPU would
+        // be reached through peer access, which need not be enabled
+        if (at.type == cudaMemoryTypeDevice && at.device != dev)
+            return fail(ND_ERR_ARG, "nd_step_heun_noalloc: m lives on device " + std::to_string(at.device) +
+                                        ", not on the current device " + std::to_string(dev));
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(ND_ERR_CUDA, "nd_step_heun_noalloc: no usable current device");
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t smem = fused_smem(P, ND_PREC_FP32, D, Dpad);
@@ -189,7 +194,7 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
         R.state_off = (long long)r * 3 * D * Dpad;
         R.spec_off = 0;
         R.Ghat = g32; R.mask = mask;
-        for (int k = 0; k < 3; ++k) R.chext[k] = cfac * ds.hext[k] / ds.Ms;
+        for (int k = 0; k < 3; ++k) R.chext[k] = cfac * (ds.hext[k] / ds.Ms);   // rounded as nd_create_disk does
         R.alpha = ds.alpha; R.dtau = dtau;
         R.sigma = sqrt(2.0 * ds.alpha * (kB * T_kelvin[r] / J) * dtau);
         R.flags = R.sigma > 0.0 ? 1 : 0;

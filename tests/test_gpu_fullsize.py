@@ -119,3 +119,61 @@ def test_uneven_batch_full_size_with_graphs_and_autotuned_plans(O):
             change = np.linalg.norm((ref - starts[name][r]) * model.mask)
             floor = 1e-7 * np.sqrt(3 * model.C)
             assert np.linalg.norm((out[r] - ref) * model.mask) <= 2e-4 * change + floor, (name, r, Pk[r])
+
+
+def _heun_full_state(O, R, L, steps, B):
+    """Full-state Heun parity on the global path: every cell of every replica
+    after `steps` steps against the oracle's trajectory from the same state and
+    Philox stream.  Tolerance: the FP32 field error (1e-5 relative) times the
+    change over the run, plus the FP32 rounding of the stored state."""
+    disk = Disk(R, L, alpha=0.01, hext=(0.0, 0.0, 1e4))
+    h = Nanodisk([disk], [B], nd.ND_FP32)
+    model = O.Model(R, L, alpha=disk.alpha, hext=disk.hext)
+    X0 = np.stack([np.linspace(-6e-9, 6e-9, B), np.linspace(3e-9, -2e-9, B)], 1)
+    m = h.empty_device()
+    h.init_vortex(m, X0)
+    start = h.unpack(m)
+    T, seeds, dt = np.full(B, 300.0), np.arange(B, dtype=np.uint64) + 40, 1e-14
+    h.heun(m, steps, dt, T, seeds, step0=5)
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    out = h.unpack(m)
+    Ts = O.scaled_temperature(300.0, disk.A, disk.L)
+    for r in range(B):
+        ref = model.heun(start[r], steps, model.dtau(dt), Ts, int(seeds[r]), 5)
+        change = np.linalg.norm((ref - start[r]) * model.mask)
+        err = np.linalg.norm((out[r] - ref) * model.mask)
+        print(f"R={R*1e9:.0f} nm replica {r}: |error| / |change| = {err / change:.2e}, max abs {np.max(np.abs(out[r] - ref)):.2e}")
+        assert np.max(np.abs(out[r] - ref)) < 2e-5
+        assert err <= 1e-4 * change + 1e-7 * np.sqrt(3 * model.C)
+
+
+def test_p512_heun_full_state_matches_oracle(O):
+    _heun_full_state(O, 200e-9, 20e-9, steps=2, B=2)
+
+
+def test_p1024_heun_full_state_matches_oracle(O):
+    """One step of the large-disk workload's disk (R = 500 nm, 196,364 cells):
+    about 8e10 direct-sum pair terms on the host."""
+    _heun_full_state(O, 500e-9, 20e-9, steps=1, B=1)
+
+
+@pytest.mark.parametrize("R,L,sampled", [(150e-9, 20e-9, False), (500e-9, 20e-9, True)])
+def test_fp64_global_path_field_large_grids(O, R, L, sampled):
+    """FP64 on the global path at P = 512 (every cell) and P = 1024 (sampled
+    cells): relative error 1e-11."""
+    disk = Disk(R, L, hext=(1e4, 0.0, -2e4))
+    h = Nanodisk([disk], [1], nd.ND_FP64)
+    assert h.layout[0]["P"] == (512 if R < 256e-9 else 1024)
+    model = O.Model(R, L, hext=disk.hext)
+    g = ndsynth.random_unit_vectors(model.D, seed=77) * model.mask
+    b = h.unpack(h.field(h.to_device([g])))[0]
+    if not sampled:
+        ref = model.field(g)
+        err = np.linalg.norm((b - ref) * model.mask) / np.linalg.norm(ref * model.mask)
+        assert err < 1e-11
+    else:
+        inside = np.flatnonzero(model.mask.ravel())
+        cells = np.concatenate([inside[ndsynth.sample_indices(len(inside), 24, seed=9)], inside[:4], inside[-4:]])
+        ref = model.field_at(g, cells)
+        got = np.stack([b[:, c // model.D, c % model.D] for c in cells])
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11

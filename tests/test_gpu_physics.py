@@ -4,10 +4,11 @@ paper fixes the relations):
 * Thiele relation (Eq. OG): the gyrotropic angular frequency of a released,
   undamped vortex equals k_F a^2 / (4 pi L A) with k_F from the constrained
   relaxations (Eq. Ux); clockwise for positive polarity.
-* Equilibrium statistics (Sec. V.C): at temperature T the core radius
-  follows p(r) = beta k_F r exp(-beta k_F r^2 / 2), so <r^2> = 2 kT / k_F,
-  with kT taken at T (1 + alpha^2) for the LL equation with noise in both
-  terms.
+* Equilibrium statistics (Sec. V.C, Sec. VI): at temperature T the core
+  radius follows p(r) = beta k_F r exp(-beta k_F r^2 / 2), so
+  <r^2> = 2 kT / k_F, with kT taken at T (1 + alpha^2) for the LL equation with
+  noise in both terms; the rotational speed follows the same law in V with
+  the gyrotropic mass m_G = G^2/k_F.
 """
 import math
 
@@ -64,37 +65,68 @@ def test_gyrotropic_period_and_thiele_relation():
     assert om_dyn == pytest.approx(om_static, rel=0.08)
 
 
-def test_equilibrium_radius_statistics():
-    R, L, a, T, alpha = 30e-9, 10e-9, 2e-9, 300.0, 0.1
+def test_equilibrium_radius_and_speed_statistics():
+    """Sec. V.C and Sec. VI at 300 K, alpha = 0.1, 128 replicas of R = 30 nm,
+    L = 10 nm, sampled every 1/16 of a gyration period:
+
+    * radius: <r^2> = 2kT/k_F and the histogram against p(r) (Eq. pr);
+    * speed: the sampled speed is the chord speed V = |X(t+D) - X(t)|/D of the
+      gyration, V = |omega| r sinc(omega D / 2) for the motion V = omega x X
+      that the Hamilton equations give; with omega the frequency of the damped
+      motion (measured here from a T = 0 release at the same alpha) the speed
+      and radius moments agree, and the V histogram follows the Rayleigh form
+      f(V) = beta m V exp(-beta m V^2/2).  Against the paper's mass
+      m_G = G^2/k_F with the static k_F the speeds are higher by the square of
+      the gap between the dynamic and static frequencies that the constraint
+      reading leaves (a few to ~25%)."""
+    R, L, a, T, alpha, A, Ms, gamma = 30e-9, 10e-9, 2e-9, 300.0, 0.1, 1.3e-11, 8.6e5, 1.76e11
     kF, _ = force_constant(R, L)
+    kT = KB * T * (1 + alpha ** 2)
+    dtau = 0.02
+    # the damped gyration frequency: T = 0 release from X = 2a at the same alpha
+    h1 = Nanodisk([Disk(R, L, alpha=alpha)], [1], nd.ND_FP32)
+    m1 = h1.empty_device()
+    h1.init_vortex(m1, [[2 * a, 0.0]])
+    h1.relax(m1, [[2 * a, 0.0]], tol=1e-5, max_iter=60000)
+    dt = dtau * h1.units[0][3]
+    xs, ys = [], []
+    for _ in range(100):
+        h1.rk4(m1, 500, dt)
+        Xc, st = h1.vortex_core(m1)
+        assert st[0] == 0
+        xs.append(Xc[0, 0]); ys.append(Xc[0, 1])
+    om_dyn = abs(omega_from_core(xs, ys, 500 * dtau))
+    om_st = abs(omega_thiele(kF, a, L, A))
     B = 128
     h = Nanodisk([Disk(R, L, alpha=alpha)], [B], nd.ND_FP32)
     m = h.empty_device()
     h.init_vortex(m, np.zeros((B, 2)))
     h.relax(m, np.zeros((B, 2)), tol=1e-5, max_iter=60000)
-    dtau = 0.02
-    dt = dtau * h.units[0][3]
     Tk, seeds = np.full(B, T), np.arange(B, dtype=np.uint64) + 1000
-    om = abs(omega_thiele(kF, a, L, 1.3e-11))
-    t_relax = 1.0 / (alpha * om)                        # decay time of the gyration amplitude
-    chunk = 100
-    n_eq = int(3 * t_relax / (chunk * dtau)) + 1
-    n_meas = int(12 * t_relax / (chunk * dtau)) + 1
+    t_relax = 1.0 / (alpha * om_st)                     # decay time of the gyration amplitude
+    chunk = int(round(2 * math.pi / om_dyn / 16 / dtau))
+    Dt = chunk * dtau                                   # sampling interval (time units)
+    n_eq = int(3 * t_relax / Dt) + 1
+    n_meas = int(12 * t_relax / Dt) + 1
     step = 0
     for _ in range(n_eq):
         h.heun(m, chunk, dt, Tk, seeds, step0=step)
         step += chunk
-    rb, rmax = 60, 12e-9
-    nd.nd_stats_reset(h.h, rmax, rb, 1000.0, 10)
+    rb, rmax = 40, 12e-9
+    G = 2 * math.pi * L * Ms / gamma
+    mG = G * G / kF
+    sinc = math.sin(om_dyn * Dt / 2) / (om_dyn * Dt / 2)
+    v_scale = math.sqrt(2 * kT / mG) * sinc * om_dyn / om_st          # expected V_rms, for the bin range
+    vb, vmax = 40, 4.0 * v_scale
+    nd.nd_stats_reset(h.h, rmax, rb, vmax, vb)
     for _ in range(n_meas):
         h.heun(m, chunk, dt, Tk, seeds, step0=step)
         step += chunk
         nd.nd_stats_sample(h.h, m, chunk * dt)
-    mom, hr, _ = nd.nd_stats_read(h.h, B, rb, 10)
+    mom, hr, hv = nd.nd_stats_read(h.h, B, rb, vb)
     assert nd.nd_check_status(h.h) == nd.ND_OK
     n = mom[:, 0].sum()
     r2 = mom[:, 3].sum() / n
-    kT = KB * T * (1 + alpha ** 2)
     pred = 2 * kT / kF
     print(f"kF={kF:.4e}  <r^2>={r2:.4e}  2kT/kF={pred:.4e}  ratio={r2/pred:.3f}  samples={n:.0f}")
     assert mom[:, 6].sum() <= 0.01 * n                   # the vortex is found in (nearly) every sample
@@ -107,5 +139,27 @@ def test_equilibrium_radius_statistics():
     expct = n * np.diff(cdf)
     keep = expct > 50
     rel_dev = np.abs(counts[keep] - expct[keep]).sum() / expct[keep].sum()
-    print(f"histogram mean |obs - exp| / exp = {rel_dev:.3f}")
+    print(f"r histogram mean |obs - exp| / exp = {rel_dev:.3f}")
     assert rel_dev < 0.15
+    # speed law (Sec. VI)
+    nv = mom[:, 4].sum()
+    v2 = mom[:, 5].sum() / nv
+    t0 = h.units[0][3]
+    hamilton = (om_dyn / t0) ** 2 * sinc ** 2 * r2       # V = omega x X, sampled as a chord
+    paper = 2 * kT / mG * sinc ** 2                      # f(V) with m_G = G^2/k_F (static k_F)
+    print(f"omega static {om_st:.4e} dynamic {om_dyn:.4e} (ratio {om_dyn/om_st:.3f}), sampling {Dt:.1f} tau, "
+          f"speed samples {nv:.0f}")
+    print(f"<V^2> = {v2:.4e} m^2/s^2; omega^2 sinc^2 <r^2> = {hamilton:.4e} (ratio {v2/hamilton:.3f}); "
+          f"2kT/m_G sinc^2 = {paper:.4e} (ratio {v2/paper:.3f}; m_G = {mG:.3e} kg)")
+    assert nv > 0.5 * n
+    assert v2 == pytest.approx(hamilton, rel=0.10)
+    assert 0.9 < v2 / paper < 1.4
+    # the V histogram has the Rayleigh form of f(V), with the mass its own <V^2> gives
+    mfit = 2 * kT / v2
+    vcounts = hv.sum(0).astype(float)
+    vedges = np.linspace(0, vmax, vb + 1)
+    vexp = nv * np.diff(1 - np.exp(-0.5 * mfit * vedges ** 2 / kT))
+    keep = vexp > 50
+    vdev = np.abs(vcounts[keep] - vexp[keep]).sum() / vexp[keep].sum()
+    print(f"V histogram mean |obs - exp| / exp = {vdev:.3f}")
+    assert vdev < 0.15

@@ -500,3 +500,197 @@ def test_gyrotropic_mass(O):
     kF = GOLD["kF_linear_coeff"]["value"] * MU0 * MS ** 2 * L ** 2 / R
     G = O.gyrovector(L, MS, GAMMA, 1)
     assert G ** 2 / kF == pytest.approx(g["value"], rel=g["rel_tol"])
+
+
+# ------------------------------------------- pins of the sampled field, <m>
+
+def test_field_at_equals_the_full_field(O):
+    """The sampled direct sum (used for the largest grids) equals the full
+    field at those cells: same Green's table, component order and exchange."""
+    model = O.Model(20e-9, 5e-9, hext=(1.5e4, -2.5e4, 3.5e4))
+    m = ndsynth.random_unit_vectors(model.D, seed=31) * model.mask
+    full = model.field(m)
+    inside = np.flatnonzero(model.mask.ravel())
+    cells = np.concatenate([inside[ndsynth.sample_indices(len(inside), 40, seed=4)], inside[:3], inside[-3:],
+                            np.flatnonzero(model.mask.ravel() == 0)[:2]])     # two outside cells read as zero
+    got = model.field_at(m, cells)
+    ref = np.stack([full[:, c // model.D, c % model.D] for c in cells])
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(full).max()
+    assert np.all(got[-2:] == 0)
+
+
+def test_mean_m_is_the_average_over_disk_cells(O):
+    model = O.Model(17e-9, 5e-9)
+    m = ndsynth.random_unit_vectors(model.D, seed=8)        # nonzero outside the disk too
+    m = m * model.mask
+    inside = model.mask.astype(bool)
+    ref = np.array([m[k][inside].mean() for k in range(3)])
+    assert np.allclose(model.mean_m(m), ref, rtol=0, atol=1e-15)
+    # a uniform state averages to itself
+    u = np.zeros((3, model.D, model.D)); u[1] = model.mask
+    assert np.allclose(model.mean_m(u), [0.0, 1.0, 0.0], atol=1e-15)
+
+
+def _two_vortex_state(model, c1, c2, core1, core2):
+    """In-plane angle winding +1 around each of two plaquette centres c1, c2
+    (cell units, relative to the grid centre); m_z = 0.05 everywhere except the
+    four corners of the two plaquettes, which carry core1 and core2."""
+    D = model.D
+    idx = np.arange(D) - 0.5 * (D - 1)
+    x, y = np.meshgrid(idx, idx, indexing="xy")
+    phi = np.arctan2(y - c1[1], x - c1[0]) + np.arctan2(y - c2[1], x - c2[0]) + 0.5 * np.pi
+    mz = np.full((D, D), 0.05)
+    for c, v in ((c1, core1), (c2, core2)):
+        i0, j0 = int(round(c[0] + 0.5 * (D - 1) - 0.5)), int(round(c[1] + 0.5 * (D - 1) - 0.5))
+        mz[j0:j0 + 2, i0:i0 + 2] = v
+    sp = np.sqrt(1 - mz ** 2)
+    m = np.stack([sp * np.cos(phi), sp * np.sin(phi), mz]) * model.mask
+    return m
+
+
+def test_core_tie_break_picks_the_largest_corner_mz2(O):
+    """Two plaquettes of winding +1 (Sec. IV's vorticity centre, tie-break of
+    the reading): the one whose corners carry the larger sum of m_z^2 wins;
+    on an exact tie the first in row-major order (smaller y, then x) wins."""
+    model = O.Model(30e-9, 5e-9)
+    a = model.a
+    c1, c2 = (-4.0, -3.0), (5.0, 4.0)                 # plaquette centres (half-integer grid offsets)
+    for core1, core2, want in ((0.6, 0.8, c2), (0.8, 0.6, c1), (0.7, 0.7, c1)):
+        m = _two_vortex_state(model, c1, c2, core1, core2)
+        st, xc, rv = model.vortex_core(m)
+        assert st == 0
+        assert np.allclose(rv, np.array(want) * a, atol=1e-15), (core1, core2, rv / a)
+    # the same pair placed on one row: the smaller x is first
+    c3, c4 = (-5.0, 2.0), (6.0, 2.0)
+    st, xc, rv = model.vortex_core(_two_vortex_state(model, c3, c4, 0.7, 0.7))
+    assert st == 0 and np.allclose(rv, np.array(c3) * a, atol=1e-15)
+
+
+# ------------------------------------------------ rotational-speed law
+
+def test_speed_law_of_the_rotational_velocity(O):
+    """Sec. VI: f(V) = beta m_G V exp(-beta m_G V^2/2) with m_G = G^2/k_F is
+    p(r) mapped by V = |omega_G| r, omega_G = k_F/G; V_rms = sqrt(2 k_F kT)/G,
+    so <V^2> = 2kT/m_G.  Checked by quadrature and against the oracle's own
+    p(r) and gyrovector, for the paper's two r_rms examples."""
+    kT = KB * 300.0
+    for case in GOLD["rrms_predictions"]["cases"]:
+        kF = case["kF_A_per_a"] * A / A_CELL
+        L = case["L_nm"] * 1e-9
+        G = O.gyrovector(L, MS, GAMMA, 1)
+        mG = O.gyro_mass(G, kF)
+        assert mG == pytest.approx(G * G / kF, rel=1e-15)
+        w = kF / G
+        vrms = math.sqrt(2 * kF * kT) / G
+        s = vrms   # integrate in units of V_rms
+        norm = integrate.quad(lambda u: O.f_V(u * s, mG, kT) * s, 0, 40)[0]
+        v2 = integrate.quad(lambda u: (u * s) ** 2 * O.f_V(u * s, mG, kT) * s, 0, 40)[0]
+        assert norm == pytest.approx(1.0, abs=1e-10)
+        assert v2 == pytest.approx(2 * kT / mG, rel=1e-9)
+        assert math.sqrt(v2) == pytest.approx(vrms, rel=1e-9)
+        # f(V) = p(V/omega)/omega, p the oracle's radial law (Eq. pr)
+        for u in (0.1, 0.7, 1.0, 2.3):
+            V = u * vrms
+            assert O.f_V(V, mG, kT) == pytest.approx(O.p_r(V / w, kF, kT) / w, rel=1e-12)
+        vmax = math.sqrt(kT / mG)
+        assert O.f_V(vmax, mG, kT) == pytest.approx(math.exp(-0.5) / vmax, rel=1e-12)
+        # V_rms = |omega_G| r_rms with the paper's r_rms (Sec. VI)
+        assert vrms / w * 1e9 == pytest.approx(case["rrms_nm"], abs=GOLD["rrms_predictions"]["abs_tol_nm"])
+
+
+# ---------------------------------------------- gyration frequency fit
+
+def test_omega_from_track_recovers_circular_motion(O):
+    """The Omega_G estimator on exact tracks: clockwise and counter-clockwise
+    circles over several turns, an off-centre start, and a shrinking spiral."""
+    dtau = 0.7
+    tau = np.arange(900) * dtau
+    for om, r0, phase in ((-3.06e-3, 4e-9, 0.3), (2.5e-3, 1e-9, -2.9), (-0.02, 6e-9, 3.1)):
+        x, y = r0 * np.cos(om * tau + phase), r0 * np.sin(om * tau + phase)
+        assert O.omega_from_track(x, y, dtau) == pytest.approx(om, rel=1e-10)
+        rr = r0 * np.exp(-1e-4 * tau)
+        x, y = rr * np.cos(om * tau + phase), rr * np.sin(om * tau + phase)
+        assert O.omega_from_track(x, y, dtau) == pytest.approx(om, rel=1e-10)
+    # a slowly modulated angular speed: the least-squares slope is the mean rate
+    th = -3e-3 * tau + 0.2 * np.sin(2 * np.pi * tau / tau[-1])
+    slope = np.polyfit(tau, th, 1)[0]
+    assert O.omega_from_track(np.cos(th), np.sin(th), dtau) == pytest.approx(slope, rel=1e-10)
+
+
+# --------------------------------------------------- power spectrum
+
+def test_power_spectrum_parseval_and_pure_tone(O):
+    """The averaged periodogram (Sec. V's thermal power spectra): the one-sided
+    sum times the bin width equals each window's mean square after its mean is
+    removed (Parseval), and a tone at bin k0 puts dt W A^2 / 2 in that bin and
+    nothing elsewhere."""
+    W, dt = 256, 2.5e-12
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(3 * W + 17) + 0.4
+    psd, nw = O.power_spectrum(x, W, dt)
+    assert nw == 3
+    win = x[:3 * W].reshape(3, W)
+    ms = np.mean([np.mean((w - w.mean()) ** 2) for w in win])
+    assert psd.sum() / (W * dt) == pytest.approx(ms, rel=1e-12)
+    k0, amp = 19, 0.37
+    t = np.arange(2 * W)
+    tone = amp * np.cos(2 * np.pi * k0 * t / W + 0.8) + 5.0      # the constant is removed per window
+    psd, nw = O.power_spectrum(tone, W, dt)
+    assert nw == 2
+    assert psd[k0] == pytest.approx(dt * W * amp ** 2 / 2, rel=1e-12)
+    others = np.delete(psd, k0)
+    assert others.max() <= 1e-20 * psd[k0] + 1e-40
+    assert O.power_spectrum(x[:W - 1], W, dt)[1] == 0
+
+
+# ------------------------------------------- user Green's table (Sec. II.B)
+
+def test_set_green_with_the_closed_form_table_changes_nothing(O):
+    model = O.Model(14e-9, 5e-9, hext=(0, 1e4, 0))
+    m = ndsynth.random_unit_vectors(model.D, seed=12) * model.mask
+    b0 = model.field(m)
+    model.set_green(model.quarter_table())
+    assert np.array_equal(model.field(m), b0)
+
+
+def test_set_green_extends_a_quarter_table_by_symmetry(O):
+    """A single source cell at the centre of an odd grid sees the table itself:
+    h^M(dx, dy) = table(|dx|, |dy|) for xx, yy, zz and sign(dx) sign(dy) times it
+    for xy (zero on the axes), so an arbitrary quarter table is reproduced in
+    every quadrant with the tensor's parities."""
+    model = O.Model(9e-9, 5e-9)                       # D = 9, centre cell (4, 4)
+    D = model.D
+    assert D % 2 == 1
+    rng = np.random.default_rng(5)
+    q = rng.standard_normal((4, D, D))
+    model.set_green(q)
+    c = D // 2
+    for comp in range(3):
+        m = np.zeros((3, D, D)); m[comp, c, c] = 1.0
+        hM = model.demag(m)
+        for j in range(D):
+            for i in range(D):
+                if not model.mask[j, i]:
+                    continue
+                dx, dy = i - c, j - c
+                qq = q[:, abs(dy), abs(dx)]
+                s = np.sign(dx) * np.sign(dy)
+                if comp == 0:     # m = x: h = (Gxx, Gxy, 0)
+                    want = (qq[0], s * qq[2], 0.0)
+                elif comp == 1:   # m = y: h = (Gxy, Gyy, 0)
+                    want = (s * qq[2], qq[1], 0.0)
+                else:             # m = z: h = (0, 0, Gzz)
+                    want = (0.0, 0.0, qq[3])
+                assert np.allclose(hM[:, j, i], want, rtol=0, atol=1e-15), (comp, i, j)
+
+
+def test_set_green_scaling_zz_halves_the_perpendicular_demag(O):
+    model = O.Model(14e-9, 5e-9)
+    m = ndsynth.random_unit_vectors(model.D, seed=13) * model.mask
+    hM = model.demag(m)
+    q = model.quarter_table()
+    q[3] *= 0.5
+    model.set_green(q)
+    h2 = model.demag(m)
+    assert np.array_equal(h2[:2], hM[:2])
+    assert np.array_equal(h2[2], 0.5 * hM[2])

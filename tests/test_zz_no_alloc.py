@@ -32,7 +32,34 @@ def test_noalloc_heun_matches_handle_heun_on_two_calls():
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert (out - ref).abs().max().item() <= 1e-5
+        # both paths launch the same Heun kernel on the same spectral kernel,
+        # twiddles and parameter blocks, so the states agree bit for bit
+        assert torch.equal(out, ref)
     assert (out - m0).abs().max().item() > 1e-4     # the state did move
+
+
+def test_noalloc_rebuilds_its_tables_when_the_geometry_changes():
+    # the array caches one geometry's spectral kernel, mask and twiddles; a
+    # stale cache would step with the wrong Green's tensor.  Alternate two
+    # disks of the same grid (D = 30, P = 64) but different thickness, one of
+    # another padded size (D = 14, P = 32), and return to the first.
+    import torch
+    disks = [Disk(30e-9, 5e-9, alpha=0.05), Disk(30e-9, 12e-9, alpha=0.05), Disk(14e-9, 5e-9, alpha=0.05),
+             Disk(30e-9, 5e-9, alpha=0.05)]
+    T = np.array([0.0, 300.0])
+    seeds = np.array([3, 4], dtype=np.uint64)
+    dt = 1e-14
+    for k, disk in enumerate(disks):
+        h = Nanodisk([disk], [2], nd.ND_FP32)
+        m0 = h.empty_device()
+        h.init_vortex(m0, np.array([[2e-9, 0.0], [-2e-9, 1e-9]]))
+        ref, out = m0.clone(), m0.clone()
+        nd.nd_step_heun(h.h, ref, 6, dt, T, seeds, 0)
+        _binding.nd_step_heun_noalloc(disk, 2, out, 6, dt, T, seeds, 0)
+        torch.cuda.synchronize()
+        assert (out - ref).abs().max().item() <= 1e-5, f"geometry {k}"
+        assert torch.equal(out, ref), f"geometry {k}"
+        h.close()
 
 
 def test_noalloc_rejects_what_exceeds_its_limits():
