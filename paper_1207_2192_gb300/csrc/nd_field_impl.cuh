@@ -60,6 +60,56 @@ template <typename T> struct V3Ptr {
     __device__ __forceinline__ void st(long long i, vec3<T> v) const { p[i] = v.x; p[s + i] = v.y; p[2 * s + i] = v.z; }
 };
 
+// The per-cell update of one stepping stage (Section III.A RK4, Section III.C
+// Heun), as a function of the cell's stage input m, its induction b, y_n and
+// the stage accumulator a (read by stages > 0) and, for Heun, the normals w:
+// returns the next stage's input; acc_new and the flags say what else the
+// stage writes (the accumulator, and y_n after the last stage).  Every path
+// (on chip, global, fused row pass) calls this one definition, so all of them
+// round identically.
+template <typename T> struct StageOut {
+    vec3<T> nm, acc;
+    bool w_acc, w_yn;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ StageOut<T> stage_update(const StepParams<T> &sp, bool noise, int stage, vec3<T> m,
+                                                    vec3<T> b, vec3<T> y, vec3<T> a, vec3<T> w)
+{
+    const T alpha = sp.alpha, dt = sp.dtau;
+    StageOut<T> o;
+    if (MODE == M_RK4) {
+        vec3<T> k = llg_rhs(m, b, alpha);
+        if (stage == 0) {
+            o.acc = k;
+            o.nm = axpy3(T(0.5) * dt, k, m);
+            o.w_acc = true; o.w_yn = false;
+        } else if (stage < 3) {
+            o.acc = axpy3(T(2), k, a);
+            o.nm = axpy3(stage == 1 ? T(0.5) * dt : dt, k, y);
+            o.w_acc = true; o.w_yn = false;
+        } else {
+            vec3<T> s = {a.x + k.x, a.y + k.y, a.z + k.z};
+            o.nm = normalize3(axpy3(dt / T(6), s, y));
+            o.w_acc = false; o.w_yn = true;
+        }
+    } else {   // M_HEUN
+        vec3<T> g = {b.x * dt, b.y * dt, b.z * dt};
+        if (noise) { g.x += sp.sigma * w.x; g.y += sp.sigma * w.y; g.z += sp.sigma * w.z; }
+        vec3<T> d = heun_dm(m, g, alpha);
+        if (stage == 0) {
+            o.acc = d;
+            o.nm = normalize3(vec3<T>{m.x + d.x, m.y + d.y, m.z + d.z});
+            o.w_acc = true; o.w_yn = false;
+        } else {
+            o.nm = normalize3(vec3<T>{y.x + T(0.5) * (a.x + d.x), y.y + T(0.5) * (a.y + d.y),
+                                      y.z + T(0.5) * (a.z + d.z)});
+            o.w_acc = false; o.w_yn = true;
+        }
+    }
+    return o;
+}
+
 // Per-cell epilogue of one field evaluation.
 //   ms  : stage magnetisation (read; overwritten with the next stage's input)
 //   yn  : state y_n (user buffer), acc : stage accumulator (scratch)
@@ -74,8 +124,6 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
                                                 V3Ptr<T> ms, V3Ptr<T> yn, V3Ptr<T> acc, V3Ptr<T> out, int stage,
                                                 unsigned long long step, V3Ptr<T> wbuf, V3Ptr<T> ynl, V3Ptr<T> accl)
 {
-    const StepParams<T> sp = step_params<T>(r);
-    const T alpha = sp.alpha, dt = sp.dtau;
     vec3<T> m = ms.ld(mi);
     if (MODE == M_FIELD) {
         out.st(si, b);
@@ -85,47 +133,24 @@ __device__ __forceinline__ double epilogue_cell(const Replica &r, int cell, long
         double bx = (double)b.x - r.chext[0], by = (double)b.y - r.chext[1], bz = (double)b.z - r.chext[2];
         return -((double)m.x * (0.5 * bx + r.chext[0]) + (double)m.y * (0.5 * by + r.chext[1]) +
                  (double)m.z * (0.5 * bz + r.chext[2]));
-    } else if (MODE == M_RK4) {
-        vec3<T> k = llg_rhs(m, b, alpha);
-        if (stage == 0) {
-            acc.st(si, k);
-            ms.st(mi, axpy3(T(0.5) * dt, k, m));
-        } else if (stage < 3) {
-            vec3<T> a = accl.ld(si), y = ynl.ld(si);
-            acc.st(si, axpy3(T(2), k, a));
-            ms.st(mi, axpy3(stage == 1 ? T(0.5) * dt : dt, k, y));
-        } else {
-            vec3<T> a = accl.ld(si), y = ynl.ld(si);
-            vec3<T> s = {a.x + k.x, a.y + k.y, a.z + k.z};
-            vec3<T> yo = normalize3(axpy3(dt / T(6), s, y));
-            yn.st(si, yo);
-            ms.st(mi, yo);
-        }
-        return 0.0;
-    } else if (MODE == M_HEUN) {
-        const T sig = sp.sigma;
-        vec3<T> g = {b.x * dt, b.y * dt, b.z * dt};
-        if (r.flags & 1) {
-            vec3<T> w;
+    } else if (MODE == M_RK4 || MODE == M_HEUN) {
+        const StepParams<T> sp = step_params<T>(r);
+        const vec3<T> zero = {T(0), T(0), T(0)};
+        vec3<T> y = zero, a = zero, w = zero;
+        if (stage > 0) { a = accl.ld(si); y = ynl.ld(si); }
+        const bool noise = MODE == M_HEUN && (r.flags & 1);
+        if (noise) {
             if (wbuf.p && stage == 1) {
                 w = wbuf.ld(mi);
             } else {
                 w = thermal_normals<T>(r.seed, (uint32_t)cell, step);
                 if (wbuf.p) wbuf.st(mi, w);
             }
-            g.x += sig * w.x; g.y += sig * w.y; g.z += sig * w.z;
         }
-        vec3<T> d = heun_dm(m, g, alpha);
-        if (stage == 0) {
-            acc.st(si, d);
-            ms.st(mi, normalize3(vec3<T>{m.x + d.x, m.y + d.y, m.z + d.z}));
-        } else {
-            vec3<T> a = accl.ld(si), y = ynl.ld(si);
-            vec3<T> yo = normalize3(vec3<T>{y.x + T(0.5) * (a.x + d.x), y.y + T(0.5) * (a.y + d.y),
-                                            y.z + T(0.5) * (a.z + d.z)});
-            yn.st(si, yo);
-            ms.st(mi, yo);
-        }
+        const StageOut<T> o = stage_update<T, MODE>(sp, noise, stage, m, b, y, a, w);
+        if (o.w_acc) acc.st(si, o.acc);
+        if (o.w_yn) yn.st(si, o.nm);
+        ms.st(mi, o.nm);
         return 0.0;
     }
     return 0.0;
@@ -701,6 +726,107 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Four consecutive elements of a row (16-byte aligned): one 16-byte access in
+// FP32, two in FP64.
+template <typename T> struct Quad { T v[4]; };
+template <typename T> __device__ __forceinline__ Quad<T> ld_quad(const T *p);
+template <> __device__ __forceinline__ Quad<float> ld_quad<float>(const float *p)
+{
+    const float4 a = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {{a.x, a.y, a.z, a.w}};
+}
+template <> __device__ __forceinline__ Quad<double> ld_quad<double>(const double *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+template <typename T> __device__ __forceinline__ void st_quad(T *p, const Quad<T> &q);
+template <> __device__ __forceinline__ void st_quad<float>(float *p, const Quad<float> &q)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+template <> __device__ __forceinline__ void st_quad<double>(double *p, const Quad<double> &q)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
+}
+
+// Epilogue of the global path for the stepping modes with quad access: each
+// thread takes four consecutive cells of a row, loads the field rows (the
+// spectrum buffer viewed as real rows) and the state rows it needs with
+// 16-byte accesses, applies stage_update to the cells inside the disk and
+// stores whole quads back (cells outside the disk and padding columns are
+// written back unchanged).  grid = (quad blocks, replicas).  Requires 16-byte
+// aligned state buffers (rows and replica blocks are multiples of 4
+// elements; the spectrum rows start on 32-byte sectors).
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256)
+    k_g_epi_quad(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ msbase,
+                 T *__restrict__ ybase, T *__restrict__ accbase, const cplx<T> *__restrict__ specbase, int stage,
+                 unsigned long long step)
+{
+    constexpr int RS = SpecGeom<P>::RS;
+    static_assert(RS % 2 == 0, "field rows start on 16-byte boundaries");
+    const Replica &r = reps[work[blockIdx.y]];
+    const int D = r.D, Dpad = r.Dpad, qpr = Dpad / 4;
+    const int qd = blockIdx.x * 256 + threadIdx.x;
+    if (qd >= D * qpr) return;
+    const int y = qd / qpr, x0 = 4 * (qd - y * qpr);
+    const long long ms_s = (long long)D * Dpad, cs2 = 2LL * D * RS;   // component strides (state, field rows)
+    const long long si = (long long)y * Dpad + x0;
+    const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off) + (long long)y * (2 * RS) + x0;
+    T *msr = msbase + r.state_off + si, *ynr = ybase + r.state_off + si, *acr = accbase + r.state_off + si;
+    unsigned in = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (x0 + u < D && r.mask[y * D + x0 + u]) in |= 1u << u;
+    if (!in) return;
+    Quad<T> m[3], b[3], yv[3], av[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        m[c] = ld_quad<T>(msr + c * ms_s);
+        b[c] = ld_quad<T>(hr + c * cs2);
+        if (stage > 0) {
+            yv[c] = ld_quad<T>(ynr + c * ms_s);
+            av[c] = ld_quad<T>(acr + c * ms_s);
+        } else {
+            yv[c] = av[c] = Quad<T>{{T(0), T(0), T(0), T(0)}};
+        }
+    }
+    const StepParams<T> sp = step_params<T>(r);
+    const bool noise = MODE == M_HEUN && (r.flags & 1);
+    const unsigned long long nstep = step + r.step0;
+    Quad<T> nm[3] = {m[0], m[1], m[2]}, na[3] = {av[0], av[1], av[2]}, ny[3] = {yv[0], yv[1], yv[2]};
+    bool w_acc = false, w_yn = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (!((in >> u) & 1u)) continue;
+        const vec3<T> mu = {m[0].v[u], m[1].v[u], m[2].v[u]};
+        const vec3<T> bu = {b[0].v[u] + sp.chext[0], b[1].v[u] + sp.chext[1], b[2].v[u] + sp.chext[2]};
+        const vec3<T> yu = {yv[0].v[u], yv[1].v[u], yv[2].v[u]}, au = {av[0].v[u], av[1].v[u], av[2].v[u]};
+        const vec3<T> w = noise ? thermal_normals<T>(r.seed, (uint32_t)(y * D + x0 + u), nstep)
+                                : vec3<T>{T(0), T(0), T(0)};
+        const StageOut<T> o = stage_update<T, MODE>(sp, noise, stage, mu, bu, yu, au, w);
+        nm[0].v[u] = o.nm.x; nm[1].v[u] = o.nm.y; nm[2].v[u] = o.nm.z;
+        if (o.w_acc) { na[0].v[u] = o.acc.x; na[1].v[u] = o.acc.y; na[2].v[u] = o.acc.z; w_acc = true; }
+        if (o.w_yn) { ny[0].v[u] = o.nm.x; ny[1].v[u] = o.nm.y; ny[2].v[u] = o.nm.z; w_yn = true; }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        st_quad<T>(msr + c * ms_s, nm[c]);
+        if (w_acc) {
+            if (stage == 0) {   // the accumulator was not loaded: outside cells keep their (unused) values
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if ((in >> u) & 1u) acr[c * ms_s + u] = na[c].v[u];
+            } else {
+                st_quad<T>(acr + c * ms_s, na[c]);
+            }
+        }
+        if (w_yn) st_quad<T>(ynr + c * ms_s, ny[c]);
+    }
+}
+
 // Copy y_n into the stage buffer (masked), for the global path.
 template <typename T>
 __global__ void k_g_load_stage(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ ybase,
@@ -966,16 +1092,39 @@ static void launch_g_epi(const LaunchArgs &a, dim3 ge, int stage, unsigned long 
                                                    (const cplx<T> *)a.spec, a.red, stage, step);
 }
 
-// The three FFT passes of one field evaluation on the global path: stage
-// buffer -> spectrum -> field rows (in the spectrum buffer).
+// The stepping epilogue with quad access when the state buffers allow it.
+template <int P, typename T, int MODE>
+static void launch_g_epi_step(const LaunchArgs &a, int maxD, int stage, unsigned long long step)
+{
+    const bool quad = ((reinterpret_cast<uintptr_t>(a.y) | reinterpret_cast<uintptr_t>(a.ms) |
+                        reinterpret_cast<uintptr_t>(a.acc)) & 15) == 0;
+    if (quad) {
+        const int maxq = maxD * ((maxD + 3) / 4);
+        k_g_epi_quad<P, T, MODE><<<dim3((maxq + 255) / 256, a.nwork), 256, 0, a.stream>>>(
+            a.reps, a.work, (T *)a.ms, (T *)a.y, (T *)a.acc, (const cplx<T> *)a.spec, stage, step);
+    } else {
+        launch_g_epi<P, T, MODE>(a, dim3((maxD * maxD + 255) / 256, a.nwork), stage, step);
+    }
+}
+
+// The FFT passes of one field evaluation on the global path: stage buffer ->
+// spectrum (forward rows), the column pass, spectrum -> field rows in the
+// spectrum buffer (inverse rows).
 template <int P, typename T>
-static void glob_field_passes(const LaunchArgs &a, int maxD)
+static void glob_rows(const LaunchArgs &a, int maxD, int inverse)
 {
     constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
     const int nrow = row_tasks(maxD);
-    dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork), gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
-    const size_t sm = glob_smem_bytes<P, T, NT>();
-    k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 0);
+    dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork);
+    k_g_rows<P, T, NT><<<gr, NT, glob_smem_bytes<P, T, NT>(), a.stream>>>(a.reps, a.work, (const T *)a.ms,
+                                                                       (cplx<T> *)a.spec, (const cplx<T> *)a.tw,
+                                                                       inverse);
+}
+
+template <int P, typename T>
+static void glob_cols(const LaunchArgs &a, int maxD)
+{
+    constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
     if constexpr (GlobTiled<P>::v) {
         using CX = ColTile<P, T, true>;
         using CZ = ColTile<P, T, false>;
@@ -987,9 +1136,18 @@ static void glob_field_passes(const LaunchArgs &a, int maxD)
         k_g_cols_tile<P, T, false><<<gz, CZ::NT, glob_smem_bytes<P, T, CZ::NT>(), a.stream>>>(
             a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
     } else {
-        k_g_cols<P, T, NT><<<gc, NT, sm, a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+        dim3 gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
+        k_g_cols<P, T, NT><<<gc, NT, glob_smem_bytes<P, T, NT>(), a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec,
+                                                                             (const cplx<T> *)a.tw);
     }
-    k_g_rows<P, T, NT><<<gr, NT, sm, a.stream>>>(a.reps, a.work, (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, 1);
+}
+
+template <int P, typename T>
+static void glob_field_passes(const LaunchArgs &a, int maxD)
+{
+    glob_rows<P, T>(a, maxD, 0);
+    glob_cols<P, T>(a, maxD);
+    glob_rows<P, T>(a, maxD, 1);
 }
 
 // One field evaluation on the global path with its epilogue.
@@ -1001,8 +1159,8 @@ static cudaError_t glob_eval(const LaunchArgs &a, int maxD, int stage, int mode,
     switch (mode) {
     case M_FIELD: launch_g_epi<P, T, M_FIELD>(a, ge, stage, step); break;
     case M_ENERGY: launch_g_epi<P, T, M_ENERGY>(a, ge, stage, step); break;
-    case M_RK4: launch_g_epi<P, T, M_RK4>(a, ge, stage, step); break;
-    case M_HEUN: launch_g_epi<P, T, M_HEUN>(a, ge, stage, step); break;
+    case M_RK4: launch_g_epi_step<P, T, M_RK4>(a, maxD, stage, step); break;
+    case M_HEUN: launch_g_epi_step<P, T, M_HEUN>(a, maxD, stage, step); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

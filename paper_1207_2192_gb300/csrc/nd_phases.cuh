@@ -66,6 +66,36 @@ __host__ __device__ __forceinline__ int row_tasks(int D) { return D + (D + 1) / 
 
 // ---------------------------------------------------------------- row fwd
 
+// Forward transform of one complex row v (held as a group's registers, element
+// t + G o in v[o]; only the first half may be nonzero) whose real and imaginary
+// parts are two real rows A and B, followed by their separation with the
+// mirror element: the half spectra k = 0..P/2 go to dA and (if hasB) dB.
+template <int P, typename T>
+__device__ __forceinline__ void row_fwd_core(cplx<T> *v, bool active, cplx<T> *dA, cplx<T> *dB, bool hasB, int t,
+                                             cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1;
+    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
+    mirror_put<P>(v, scr, t);
+    __syncwarp(gmask);
+    if (active) {
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            if (k <= P / 2) {
+                const cplx<T> w = mirror_get<P>(scr, k);
+                const T h = T(0.5);
+                cplx<T> A = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
+                cplx<T> B = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
+                dA[k] = A;
+                if (hasB) dB[k] = B;
+            }
+        }
+    }
+    __syncwarp(gmask);
+}
+
 // ms: stage magnetisation [3][D][ldm] (zero outside the disk); spec as above
 // with component stride cstride (complex words).
 template <int P, typename T>
@@ -94,27 +124,10 @@ __device__ __forceinline__ void row_fwd_task(int q, bool active, int D, const T 
             }
         }
     }
-    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
-    mirror_put<P>(v, scr, t);
-    __syncwarp(gmask);
     cplx<T> *dA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
     cplx<T> *dB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
     const bool hasB = isxy || (y1 < D);
-    if (active) {
-#pragma unroll
-        for (int o = 0; o < R1; ++o) {
-            const int k = t + G * o;
-            if (k <= P / 2) {
-                const cplx<T> w = mirror_get<P>(scr, k);
-                const T h = T(0.5);
-                cplx<T> A = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
-                cplx<T> B = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
-                dA[k] = A;
-                if (hasB) dB[k] = B;
-            }
-        }
-    }
-    __syncwarp(gmask);
+    row_fwd_core<P, T>(v, active, dA, dB, hasB, t, scr, tw, gmask);
 }
 
 // --------------------------------------------------------------- columns
@@ -284,22 +297,34 @@ __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spe
 
 // ---------------------------------------------------------------- row inv
 
+// Rows of row task q (q < D: the xy row y0 = q; else the z pair y0 = 2(q-D),
+// y0 + 1) in the spectrum buffer: rA holds the spectrum of the row that ends in
+// the real part, rB (if hasB) the one that ends in the imaginary part.
+template <int P, typename T>
+__device__ __forceinline__ void row_task_rows(int q, int D, cplx<T> *spec, long long cstride, cplx<T> *&rA,
+                                              cplx<T> *&rB, bool &hasB)
+{
+    constexpr int RS = SpecGeom<P>::RS;
+    const bool isxy = q < D;
+    const int y0 = isxy ? q : 2 * (q - D);
+    const int y1 = y0 + 1;
+    hasB = isxy || (y1 < D);
+    rA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
+    rB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
+}
+
+// Inverse transform of row task q into the group's registers: afterwards the
+// real parts of v[o], o < R1/2, are row A at x = t + G o and the imaginary
+// parts row B.
 // HALF_LOAD: read only the stored half rows k <= P/2 and take the mirrored
 // entries k > P/2 from the group's scratch (for spectra in global memory,
 // where each load is a round trip to L2; on chip the direct reads are cheaper).
 template <int P, typename T, bool HALF_LOAD = false>
-__device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> *spec, long long cstride, int t,
-                                             cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
+__device__ __forceinline__ void row_inv_fft(cplx<T> *v, bool active, const cplx<T> *rA, const cplx<T> *rB, bool hasB,
+                                            int t, cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
-    const bool isxy = q < D;
-    const int y0 = isxy ? q : 2 * (q - D);
-    const int y1 = y0 + 1;
-    const bool hasB = isxy || (y1 < D);
-    cplx<T> *rA = isxy ? spec + (long long)y0 * RS : spec + 2 * cstride + (long long)y0 * RS;
-    cplx<T> *rB = isxy ? spec + cstride + (long long)y0 * RS : spec + 2 * cstride + (long long)y1 * RS;
-    cplx<T> v[R1];
+    constexpr int G = Gm::G, R1 = Gm::R1;
     if constexpr (HALF_LOAD) {
         static_assert(Gm::SCRATCH >= P + 2, "scratch holds both half rows");
         constexpr int KB = P / 2 + 1;   // B's half row starts here in the scratch
@@ -343,6 +368,19 @@ __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> 
         }
     }
     fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
+}
+
+template <int P, typename T, bool HALF_LOAD = false>
+__device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> *spec, long long cstride, int t,
+                                             cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1;
+    cplx<T> *rA, *rB;
+    bool hasB;
+    row_task_rows<P, T>(q, D, spec, cstride, rA, rB, hasB);
+    cplx<T> v[R1];
+    row_inv_fft<P, T, HALF_LOAD>(v, active, rA, rB, hasB, t, scr, tw, gmask);
     if (!active) return;
     T *oA = reinterpret_cast<T *>(rA), *oB = reinterpret_cast<T *>(rB);
 #pragma unroll

@@ -2,7 +2,10 @@
 configuration the benchmark times.
 
 * Large disk (R = 500 nm, P = 1024, global path) and R = 200 nm (P = 512):
-  the field on sampled cells against the oracle's direct sum at those cells.
+  the field on sampled cells against the oracle's direct sum at those cells;
+  full-state Heun trajectories (every cell: two steps at P = 512, one at
+  P = 1024) against the oracle's; FP64 fields at P = 512 (every cell) and
+  P = 1024 (sampled cells).
 * Batched Heun, 256 replicas of R = 50 nm (time-sliced schedule over the
   SMs): sampled replicas against the oracle's Heun trajectory.
 """
@@ -144,7 +147,7 @@ def _heun_full_state(O, R, L, steps, B):
         err = np.linalg.norm((out[r] - ref) * model.mask)
         print(f"R={R*1e9:.0f} nm replica {r}: |error| / |change| = {err / change:.2e}, max abs {np.max(np.abs(out[r] - ref)):.2e}")
         assert np.max(np.abs(out[r] - ref)) < 2e-5
-        assert err <= 1e-4 * change + 1e-7 * np.sqrt(3 * model.C)
+        assert err <= 5e-5 * change + 1e-7 * np.sqrt(3 * model.C)
 
 
 def test_p512_heun_full_state_matches_oracle(O):
