@@ -128,6 +128,30 @@ int nd_set_green_tensor(nd_handle *h, int d, const double *Gq);
 /* Per-replica damping alpha (host array [B]); replaces the disks' values. */
 int nd_set_damping(nd_handle *h, const double *alpha);
 
+/* Variant of the geometry (Sec. II.A's element, not necessarily circular):
+ * replace disk d's mask by any set of cells of its D x D grid.  mask is a host
+ * array [D][D] (row j = y index, column i = x index), nonzero inside.  The grid
+ * D, the padded size P and the spectral kernel stay (the kernel does not depend
+ * on the mask, and the exchange folded into it stays exact because cells
+ * outside the mask hold zero); every later call -- field, energy, stepping,
+ * relaxation, core estimator, statistics -- uses the new cell set, and
+ * nd_replica_layout / nd_units report its cell count.  State values outside
+ * the new mask are ignored and left unchanged.  Synchronises the device. */
+int nd_set_mask(nd_handle *h, int d, const unsigned char *mask);
+
+/* Time-dependent external field (Sec. II.A's H_ext switched per time step: a
+ * pulse, or any schedule): step s of the stepping calls uses H_ext = H[s]
+ * (host array [n_steps][3], A/m) for all stages of that step while
+ * s < n_steps, and the disk's static hext afterwards.  The step index s is the
+ * Heun noise counter (step0 + k in nd_step_heun and in graphs) and, for RK4,
+ * a counter of the handle that starts at 0 when the schedule is set and
+ * advances by n_steps with every nd_step_rk4 call (RK4 graphs use their
+ * step0 argument and advance it per replay), so a run split over several
+ * calls sees the same field as one call.  nd_effective_field, nd_energy and
+ * nd_relax_constrained use the static field.  n_steps = 0 removes the
+ * schedule.  Synchronises the device. */
+int nd_set_field_schedule(nd_handle *h, int d, long long n_steps, const double *H);
+
 /* b <- effective induction of Eq. Bi for every replica's state m:
  * b_i = sum_{j in z(i), j in disk} m_j + (a^2/lambda_ex^2)(h_ext + h^M_i).
  * b has the state layout; cells outside the disks are written as zero. */

@@ -84,6 +84,9 @@ def lib():
                 "ndo_model_mask": (None, [_P, _P]),
                 "ndo_model_set_alpha": (None, [_P, _D]),
                 "ndo_model_set_green": (None, [_P, _P]),
+                "ndo_model_set_mask": (_I, [_P, _P]),
+                "ndo_model_set_schedule": (_I, [_P, ctypes.c_long, _P, _D]),
+                "ndo_rk4_at": (None, [_P, _P, ctypes.c_long, _D, ctypes.c_uint64]),
                 "ndo_demag": (None, [_P, _P, _P]),
                 "ndo_field": (None, [_P, _P, _P]),
                 "ndo_field_parts": (None, [_P, _P, _P, _P]),
@@ -304,10 +307,26 @@ class Model:
         lib().ndo_llg_rhs(self._buf, _ptr(m), _ptr(b), alpha, _ptr(f))
         return f
 
-    def rk4(self, m, nsteps, dtau):
+    def rk4(self, m, nsteps, dtau, step0=0):
+        """RK4 steps step0 .. step0 + nsteps - 1 (the index selects a scheduled field)."""
         m = self._state(m).copy()
-        lib().ndo_rk4(self._buf, _ptr(m), nsteps, dtau)
+        lib().ndo_rk4_at(self._buf, _ptr(m), nsteps, dtau, step0)
         return m
+
+    def set_mask(self, mask):
+        """Replace the disk mask by any cell set of the D x D grid."""
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        assert mk.shape == (self.D, self.D)
+        self.C = lib().ndo_model_set_mask(self._buf, _ptr(mk))
+        lib().ndo_model_mask(self._buf, _ptr(self.mask))
+
+    def set_schedule(self, hs):
+        """Per-step external field H_ext(s) in A/m, shape (n, 3); None clears."""
+        if hs is None:
+            lib().ndo_model_set_schedule(self._buf, 0, None, self.Ms)
+            return
+        hs = np.ascontiguousarray(hs, dtype=np.float64).reshape(-1, 3)
+        lib().ndo_model_set_schedule(self._buf, len(hs), _ptr(hs), self.Ms)
 
     def heun(self, m, nsteps, dtau, Ts, seed, step0=0):
         m = self._state(m).copy()

@@ -55,6 +55,8 @@ typedef struct {
     int polarity, chirality;
     unsigned char *mask;   /* [D][D] */
     double *Gt;            /* a^2 G at displacement (dx, dy) cells: [4][2D-1][2D-1], comps xx, yy, xy, zz */
+    double *sched;         /* optional per-step external field H_ext(s)/Ms, [nsched][3] */
+    long nsched;
 } ndo_model;
 
 /* ------------------------------------------------------------------ units */
@@ -271,8 +273,44 @@ void ndo_model_set_green(ndo_model *m, const double *Gq)
 
 void ndo_model_free(ndo_model *m)
 {
-    free(m->mask); free(m->Gt);
-    m->mask = NULL; m->Gt = NULL;
+    free(m->mask); free(m->Gt); free(m->sched);
+    m->mask = NULL; m->Gt = NULL; m->sched = NULL; m->nsched = 0;
+}
+
+/* Replace the disk mask by any set of cells of the D x D grid (a variant of
+ * the geometry of Sec. II.A: a non-circular element); mask is [D][D], nonzero
+ * inside.  The Green's table does not depend on the mask.  Returns the new
+ * number of cells. */
+int ndo_model_set_mask(ndo_model *m, const unsigned char *mask)
+{
+    const int N = m->D * m->D;
+    int C = 0;
+    for (int t = 0; t < N; ++t) { m->mask[t] = mask[t] ? 1 : 0; C += m->mask[t]; }
+    m->C = C;
+    return C;
+}
+
+/* A time-dependent external field (Sec. II.A's H_ext, switched per time step:
+ * a pulse or any other schedule): step s of a trajectory (the steppers'
+ * global step index) uses H_ext = hs[s] (A/m, [n][3]) for all of its stages
+ * while s < n, and the static field of the disk afterwards.  n = 0 clears. */
+int ndo_model_set_schedule(ndo_model *m, long n, const double *hs, double Ms)
+{
+    free(m->sched);
+    m->sched = NULL;
+    m->nsched = 0;
+    if (n <= 0) return 0;
+    m->sched = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!m->sched) return -1;
+    for (long i = 0; i < 3 * n; ++i) m->sched[i] = hs[i] / Ms;
+    m->nsched = n;
+    return 0;
+}
+
+/* The scaled external field H_ext/Ms of step s. */
+static const double *step_field(const ndo_model *m, uint64_t s)
+{
+    return (m->sched && s < (uint64_t)m->nsched) ? m->sched + 3 * s : m->h;
 }
 
 int ndo_model_D(const ndo_model *m) { return m->D; }
@@ -332,9 +370,9 @@ static void exchange_sum(const ndo_model *m, const double *mv, int t, double out
     }
 }
 
-/* Dimensionless effective induction (Eq. Bi):
+/* Dimensionless effective induction (Eq. Bi) with the scaled external field hx:
  *   b_i = sum_{j in z(i)} m_j + (a^2/lambda_ex^2) (h_ext + h^M_i). */
-void ndo_field(const ndo_model *m, const double *mv, double *b)
+static void field_h(const ndo_model *m, const double *mv, double *b, const double hx[3])
 {
     const int N = m->D * m->D;
     ndo_demag(m, mv, b);
@@ -342,9 +380,12 @@ void ndo_field(const ndo_model *m, const double *mv, double *b)
         if (!m->mask[t]) { b[t] = b[N + t] = b[2 * N + t] = 0.0; continue; }
         double ex[3];
         exchange_sum(m, mv, t, ex);
-        for (int k = 0; k < 3; ++k) b[k * N + t] = ex[k] + m->c * (m->h[k] + b[k * N + t]);
+        for (int k = 0; k < 3; ++k) b[k * N + t] = ex[k] + m->c * (hx[k] + b[k * N + t]);
     }
 }
+
+/* Eq. Bi with the disk's static external field. */
+void ndo_field(const ndo_model *m, const double *mv, double *b) { field_h(m, mv, b, m->h); }
 
 /* Effective induction at selected cells only (flat indices j*D+i), by the
  * same direct sum: for sampled checks of large grids.  out is [n][3]. */
@@ -457,17 +498,19 @@ static void normalize_all(const ndo_model *m, double *mv)
 /* Classical fourth-order Runge-Kutta for the LLG equation with the full field
  * evaluated at all four stages (Section III.A); |m_i| = 1 restored after each
  * full step (the paper is silent on renormalisation; this is the reading the
- * CUDA path follows too).  dtau is the dimensionless step gamma B0 dt. */
-void ndo_rk4(const ndo_model *m, double *mv, long nsteps, double dtau)
+ * CUDA path follows too).  dtau is the dimensionless step gamma B0 dt; the
+ * steps are numbered from step0 (the index selects a scheduled field). */
+void ndo_rk4_at(const ndo_model *m, double *mv, long nsteps, double dtau, uint64_t step0)
 {
     const int N3 = 3 * m->D * m->D;
     double *b = malloc(sizeof(double) * N3), *k = malloc(sizeof(double) * N3),
            *acc = malloc(sizeof(double) * N3), *ys = malloc(sizeof(double) * N3);
     static const double wstage[3] = {0.5, 0.5, 1.0};
     for (long n = 0; n < nsteps; ++n) {
+        const double *hx = step_field(m, step0 + (uint64_t)n);   /* one external field per step */
         memcpy(ys, mv, sizeof(double) * N3);
         for (int s = 0; s < 4; ++s) {
-            ndo_field(m, ys, b);
+            field_h(m, ys, b, hx);
             ndo_llg_rhs(m, ys, b, m->alpha, k);
             for (int t = 0; t < N3; ++t) {
                 acc[t] = (s == 0) ? k[t] : acc[t] + ((s == 3) ? 1.0 : 2.0) * k[t];
@@ -479,6 +522,9 @@ void ndo_rk4(const ndo_model *m, double *mv, long nsteps, double dtau)
     }
     free(b); free(k); free(acc); free(ys);
 }
+
+/* RK4 steps numbered from 0 (the step index selects a scheduled field). */
+void ndo_rk4(const ndo_model *m, double *mv, long nsteps, double dtau) { ndo_rk4_at(m, mv, nsteps, dtau, 0); }
 
 /* ---------------------------------------------------- noise generator */
 
@@ -546,7 +592,8 @@ static inline void heun_dm(const double mm[3], const double bb[3], const double 
  * Euler predictor y~ = y + dm(y), corrector y' = y + (dm(y) + dm(y~))/2 with
  * the same random vector w_n in both stages; |m| = 1 restored after the
  * predictor and after the corrector.  Ts is kT/J; step0 is the global index of
- * the first step (the noise counter). */
+ * the first step (the noise counter, which also selects a scheduled external
+ * field). */
 void ndo_heun(const ndo_model *m, double *mv, long nsteps, double dtau, double Ts,
               uint64_t seed, uint64_t step0)
 {
@@ -556,12 +603,13 @@ void ndo_heun(const ndo_model *m, double *mv, long nsteps, double dtau, double T
            *yp = malloc(sizeof(double) * 3 * N), *W = malloc(sizeof(double) * 3 * N);
     for (long n = 0; n < nsteps; ++n) {
         uint64_t step = step0 + (uint64_t)n;
+        const double *hx = step_field(m, step);   /* one external field per step */
         for (int t = 0; t < N; ++t) {
             double w[3] = {0, 0, 0};
             if (sig > 0.0) ndo_thermal_normals(seed, (uint32_t)t, step, w);
             for (int k = 0; k < 3; ++k) W[k * N + t] = w[k];
         }
-        ndo_field(m, mv, b);
+        field_h(m, mv, b, hx);
         for (int t = 0; t < N; ++t) {
             double mm[3] = {mv[t], mv[N + t], mv[2 * N + t]}, bb[3] = {b[t], b[N + t], b[2 * N + t]};
             double w[3] = {W[t], W[N + t], W[2 * N + t]}, d[3];
@@ -569,7 +617,7 @@ void ndo_heun(const ndo_model *m, double *mv, long nsteps, double dtau, double T
             for (int k = 0; k < 3; ++k) { dm1[k * N + t] = d[k]; yp[k * N + t] = mm[k] + d[k]; }
         }
         normalize_all(m, yp);
-        ndo_field(m, yp, b);
+        field_h(m, yp, b, hx);
         for (int t = 0; t < N; ++t) {
             double mm[3] = {yp[t], yp[N + t], yp[2 * N + t]}, bb[3] = {b[t], b[N + t], b[2 * N + t]};
             double w[3] = {W[t], W[N + t], W[2 * N + t]}, d[3];

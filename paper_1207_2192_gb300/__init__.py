@@ -18,11 +18,12 @@ from ._binding import (ND_METHOD_HEUN, ND_METHOD_RK4, nd_autotune, nd_plan_info,
                        ND_FP32, ND_FP64, ND_OK, NDError, nd_create_disk, nd_destroy, nd_disk_desc, nd_disk_mask,
                        nd_effective_field, nd_energy, nd_get_info, nd_init_vortex, nd_last_error, nd_mean_m,
                        nd_relax_constrained, nd_replica_layout, nd_set_damping, nd_set_green_tensor, nd_step_heun,
+                       nd_set_mask, nd_set_field_schedule,
                        nd_stats_read, nd_stats_reset, nd_stats_sample, nd_step_rk4, nd_units, nd_vortex_core)
 
 __all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "nd_create_disk", "nd_destroy", "nd_effective_field",
            "nd_energy", "nd_step_rk4", "nd_step_heun", "nd_init_vortex", "nd_vortex_core", "nd_mean_m",
-           "nd_set_green_tensor", "nd_set_damping", "nd_units", "nd_replica_layout", "nd_get_info",
+           "nd_set_green_tensor", "nd_set_damping", "nd_set_mask", "nd_set_field_schedule", "nd_units", "nd_replica_layout", "nd_get_info",
            "nd_disk_mask", "nd_last_error", "nd_relax_constrained",
            "nd_stats_reset", "nd_stats_sample", "nd_stats_read", "nd_check_status", "nd_selftest_handover_timeout",
            "nd_series_reset", "nd_series_sample", "nd_series_read", "nd_power_spectrum", "ND_GRAPH_STATS", "ND_GRAPH_SERIES",
@@ -155,6 +156,16 @@ class Nanodisk:
 
     def set_green_tensor(self, d, Gq=None):
         nd_set_green_tensor(self.h, d, Gq)
+
+    def set_mask(self, d, mask):
+        """Replace disk d's mask by any cell set of its grid (refreshes the layout)."""
+        nd_set_mask(self.h, d, mask)
+        self.layout = [nd_replica_layout(self.h, r) for r in range(self.B)]
+        self.units = [nd_units(self.h, k) for k in range(len(self.disks))]
+
+    def set_field_schedule(self, d, H=None):
+        """Per-step external field H[s] in A/m, shape (n, 3); None removes it."""
+        nd_set_field_schedule(self.h, d, H)
 
     def dtau(self, dt_seconds, d=0):
         return dt_seconds / self.units[d][3]

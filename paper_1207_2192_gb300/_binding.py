@@ -52,6 +52,8 @@ SIGNATURES = {
     "nd_units": (_I, [_P, _I, _P]),
     "nd_set_green_tensor": (_I, [_P, _I, _P]),
     "nd_set_damping": (_I, [_P, _P]),
+    "nd_set_mask": (_I, [_P, _I, _P]),
+    "nd_set_field_schedule": (_I, [_P, _I, _LL, _P]),
     "nd_effective_field": (_I, [_P, _P, _P, _P]),
     "nd_energy": (_I, [_P, _P, _P, _P, _P]),
     "nd_step_rk4": (_I, [_P, _P, _LL, _D, _P]),
@@ -181,6 +183,20 @@ def nd_set_green_tensor(h, d, Gq=None):
 def nd_set_damping(h, alpha):
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     _check(lib().nd_set_damping(h, _ptr(a)))
+
+
+def nd_set_mask(h, d, mask):
+    mk = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(lib().nd_set_mask(h, d, _ptr(mk)))
+
+
+def nd_set_field_schedule(h, d, H=None):
+    """Per-step external field H[s] (A/m, shape (n, 3)); None removes it."""
+    if H is None:
+        _check(lib().nd_set_field_schedule(h, d, 0, None))
+        return
+    Ha = np.ascontiguousarray(H, dtype=np.float64).reshape(-1, 3)
+    _check(lib().nd_set_field_schedule(h, d, len(Ha), _ptr(Ha)))
 
 
 def nd_effective_field(h, m, b, stream=None):

@@ -46,6 +46,10 @@ struct DiskInfo {
     float *ghat32 = nullptr;
     double *ghatL = nullptr;   // thickness derivative of the demagnetisation kernel (FP64)
     double dNx = 0, dNz = 0;   // dN/d(L/a) of the self terms
+    // per-step external field schedule, (a^2/lambda^2) H_ext(s)/Ms, [nsched][3]
+    float *sched32 = nullptr;
+    double *sched64 = nullptr;
+    long long nsched = 0;
 };
 
 struct SizeClass {
@@ -137,6 +141,7 @@ struct nd_handle {
     int n_sm = 0;
     int *flags_d = nullptr;               // [B] replica hand-over flags of the time-sliced schedule
     unsigned *status_d = nullptr;         // device status word (ND_DEV_* bits)
+    unsigned long long rk4_step = 0;      // step index of the next nd_step_rk4 step (field schedules)
 };
 
 static int setup_class_paths(nd_handle *h)
@@ -197,6 +202,9 @@ static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const d
         R.falpha = (float)R.alpha;
         R.fdtau = (float)R.dtau;
         R.fsigma = (float)R.sigma;
+        R.fsched = table == TAB_DL ? nullptr : d.sched32;
+        R.dsched = table == TAB_DL ? nullptr : d.sched64;
+        R.nsched = table == TAB_DL ? 0 : d.nsched;
     }
 }
 
@@ -535,7 +543,10 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
 void nd_destroy(nd_handle *h)
 {
     if (!h) return;
-    for (auto &d : h->disks) { cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL); }
+    for (auto &d : h->disks) {
+        cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL);
+        cudaFree(d.sched32); cudaFree(d.sched64);
+    }
     for (auto &c : h->classes) { cudaFree(c.work_d); cudaFree(c.segs_d); cudaFree(c.seg_off_d); }
     cudaFree(h->flags_d);
     cudaFree(h->status_d);
@@ -635,6 +646,49 @@ int nd_set_green_tensor(nd_handle *h, int d, const double *Gq)
     return ND_OK;
 }
 
+int nd_set_mask(nd_handle *h, int d, const unsigned char *mask)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (d < 0 || d >= (int)h->disks.size() || !mask) return fail(ND_ERR_ARG, "bad disk index or null mask");
+    DiskInfo &di = h->disks[d];
+    int C = 0;
+    for (size_t i = 0; i < di.mask.size(); ++i) {
+        di.mask[i] = mask[i] ? 1 : 0;
+        C += di.mask[i];
+    }
+    di.C = C;
+    ND_CUDA(cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice));
+    return ND_OK;
+}
+
+int nd_set_field_schedule(nd_handle *h, int d, long long n_steps, const double *H)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (d < 0 || d >= (int)h->disks.size()) return fail(ND_ERR_ARG, "bad disk index");
+    if (n_steps < 0 || (n_steps > 0 && !H)) return fail(ND_ERR_ARG, "need n_steps >= 0 and a field array");
+    DiskInfo &di = h->disks[d];
+    ND_CUDA(cudaDeviceSynchronize());   // kernels in flight may still read the old schedule
+    cudaFree(di.sched32);
+    cudaFree(di.sched64);
+    di.sched32 = nullptr;
+    di.sched64 = nullptr;
+    di.nsched = 0;
+    h->rk4_step = 0;
+    if (n_steps == 0) return ND_OK;
+    std::vector<double> v64(3 * (size_t)n_steps);
+    std::vector<float> v32(3 * (size_t)n_steps);
+    for (size_t i = 0; i < v64.size(); ++i) {
+        v64[i] = di.cfac * (H[i] / di.desc.Ms);   // rounded as the static field is
+        v32[i] = (float)v64[i];
+    }
+    ND_CUDA(cudaMalloc(&di.sched64, sizeof(double) * v64.size()));
+    ND_CUDA(cudaMalloc(&di.sched32, sizeof(float) * v32.size()));
+    ND_CUDA(cudaMemcpy(di.sched64, v64.data(), sizeof(double) * v64.size(), cudaMemcpyHostToDevice));
+    ND_CUDA(cudaMemcpy(di.sched32, v32.data(), sizeof(float) * v32.size(), cudaMemcpyHostToDevice));
+    di.nsched = n_steps;
+    return ND_OK;
+}
+
 int nd_set_damping(nd_handle *h, const double *alpha)
 {
     if (int rc = check_handle(h)) return rc;
@@ -704,9 +758,10 @@ int nd_step_rk4(nd_handle *h, void *m, long long n_steps, double dt_seconds, voi
     void *md = nullptr;
     if (int rc = stage_in(h, m, &md, true, st, &h->stage_in)) return rc;
     if (n_steps > 0) {
-        fill_reps(h, h->prec == ND_FP64, dt_seconds, nullptr, nullptr, 0);
+        fill_reps(h, h->prec == ND_FP64, dt_seconds, nullptr, nullptr, h->rk4_step);
         upload_reps(h, st);
         if (int rc = run_mode(h, M_RK4, false, md, nullptr, n_steps, st)) return rc;
+        h->rk4_step += (unsigned long long)n_steps;
     }
     return stage_out(h, m, md, st);
 }

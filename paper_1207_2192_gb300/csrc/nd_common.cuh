@@ -101,6 +101,12 @@ struct Replica {
     unsigned long long seed, step0;
     float fchext[3];             // single-precision copies for the FP32 kernels
     float falpha, fdtau, fsigma;
+    // optional per-step external field (a pulse or any schedule): step s of
+    // the stepping modes uses (a^2/lambda^2) H_ext(s)/Ms = sched[3 s ..] while
+    // s < nsched, else chext; one array per kernel precision (null: none)
+    const float *fsched;
+    const double *dsched;
+    long long nsched;
 };
 
 // Stepping parameters in the kernel's precision (no double arithmetic in the
@@ -114,6 +120,23 @@ template <> __device__ __forceinline__ StepParams<float> step_params<float>(cons
 template <> __device__ __forceinline__ StepParams<double> step_params<double>(const Replica &r)
 {
     return {{r.chext[0], r.chext[1], r.chext[2]}, r.alpha, r.dtau, r.sigma};
+}
+
+// The scaled external field (a^2/lambda^2) H_ext/Ms of step s of a stepping
+// call: the disk's schedule while s < nsched, else the static field.
+template <typename T> __device__ __forceinline__ vec3<T> step_chext(const Replica &r, const StepParams<T> &sp,
+                                                                    unsigned long long s);
+template <> __device__ __forceinline__ vec3<float> step_chext<float>(const Replica &r, const StepParams<float> &sp,
+                                                                      unsigned long long s)
+{
+    if (r.fsched && s < (unsigned long long)r.nsched) return {r.fsched[3 * s], r.fsched[3 * s + 1], r.fsched[3 * s + 2]};
+    return {sp.chext[0], sp.chext[1], sp.chext[2]};
+}
+template <> __device__ __forceinline__ vec3<double> step_chext<double>(const Replica &r, const StepParams<double> &sp,
+                                                                        unsigned long long s)
+{
+    if (r.dsched && s < (unsigned long long)r.nsched) return {r.dsched[3 * s], r.dsched[3 * s + 1], r.dsched[3 * s + 2]};
+    return {sp.chext[0], sp.chext[1], sp.chext[2]};
 }
 
 // Per-replica inputs and outputs of the constrained relaxation.

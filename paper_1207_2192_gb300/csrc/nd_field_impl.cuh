@@ -451,12 +451,15 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
                         accl = V3Ptr<T>{reinterpret_cast<T *>(scratch) + 3 * ms_s, ms_s};
                     }
                 }
+                // the external field of this step (a scheduled one in the stepping modes)
+                const vec3<T> cx = (MODE == M_RK4 || MODE == M_HEUN) ? step_chext<T>(r, sp, step)
+                                                                     : vec3<T>{sp.chext[0], sp.chext[1], sp.chext[2]};
                 for (int cell = tid; cell < DD; cell += NT) {
                     if (!r.mask[cell]) continue;
                     const int y = cell / D, x = cell - y * D;
                     const long long si = (long long)y * Dpad + x;
                     const long long hi = (long long)y * (2 * RS) + x;
-                    vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+                    vec3<T> b = {hr[hi] + cx.x, hr[2 * cs + hi] + cx.y, hr[4 * cs + hi] + cx.z};
                     if (MODE == M_ENERGY)
                         esum += epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step);
                     else
@@ -708,7 +711,9 @@ __global__ void __launch_bounds__(256)
         const T *hr = reinterpret_cast<const T *>(specbase + r.spec_off);
         const long long hi = (long long)y * (2 * RS) + x;
         const StepParams<T> sp = step_params<T>(r);
-        vec3<T> b = {hr[hi] + sp.chext[0], hr[2 * cs + hi] + sp.chext[1], hr[4 * cs + hi] + sp.chext[2]};
+        const vec3<T> cx = (MODE == M_RK4 || MODE == M_HEUN) ? step_chext<T>(r, sp, step + r.step0)
+                                                             : vec3<T>{sp.chext[0], sp.chext[1], sp.chext[2]};
+        vec3<T> b = {hr[hi] + cx.x, hr[2 * cs + hi] + cx.y, hr[4 * cs + hi] + cx.z};
         V3Ptr<T> ms{msbase + r.state_off, ms_s}, yn{ybase + r.state_off, ms_s};
         V3Ptr<T> acc{accbase ? accbase + r.state_off : nullptr, ms_s}, out{outbase ? outbase + r.state_off : nullptr, ms_s};
         e = epilogue_cell<T, MODE>(r, cell, si, si, b, ms, yn, acc, out, stage, step + r.step0);
@@ -796,13 +801,14 @@ __global__ void __launch_bounds__(256)
     const StepParams<T> sp = step_params<T>(r);
     const bool noise = MODE == M_HEUN && (r.flags & 1);
     const unsigned long long nstep = step + r.step0;
+    const vec3<T> cx = step_chext<T>(r, sp, nstep);
     Quad<T> nm[3] = {m[0], m[1], m[2]}, na[3] = {av[0], av[1], av[2]}, ny[3] = {yv[0], yv[1], yv[2]};
     bool w_acc = false, w_yn = false;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         if (!((in >> u) & 1u)) continue;
         const vec3<T> mu = {m[0].v[u], m[1].v[u], m[2].v[u]};
-        const vec3<T> bu = {b[0].v[u] + sp.chext[0], b[1].v[u] + sp.chext[1], b[2].v[u] + sp.chext[2]};
+        const vec3<T> bu = {b[0].v[u] + cx.x, b[1].v[u] + cx.y, b[2].v[u] + cx.z};
         const vec3<T> yu = {yv[0].v[u], yv[1].v[u], yv[2].v[u]}, au = {av[0].v[u], av[1].v[u], av[2].v[u]};
         const vec3<T> w = noise ? thermal_normals<T>(r.seed, (uint32_t)(y * D + x0 + u), nstep)
                                 : vec3<T>{T(0), T(0), T(0)};

@@ -2,8 +2,9 @@
 thermal spectra of <m_x> whose peaks give the gyrotropic frequency).
 
 * A series of prescribed uniform states: the recorded <m> equals the
-  prescribed values, and the averaged periodogram equals numpy's FFT of the
-  prescribed series under the same definition.
+  prescribed values, and the averaged periodogram equals the FP64 oracle's
+  (a direct DFT of each window, pinned by Parseval and a pure tone) and
+  numpy's FFT of the prescribed series under the same definition.
 * Graph replays with ND_GRAPH_SERIES append one sample each, equal to <m>.
 * Physics: the peak of the <m_y> spectrum of a released undamped vortex is
   the gyrotropic frequency of its core trajectory in the same run.
@@ -34,7 +35,7 @@ def numpy_psd(x, window, dt):
     return psd, np.arange(window // 2 + 1) / (window * dt)
 
 
-def test_power_spectrum_of_prescribed_series_matches_numpy():
+def test_power_spectrum_of_prescribed_series_matches_oracle(O):
     disk = Disk(10e-9, 3e-9)
     h = Nanodisk([disk], [2], nd.ND_FP32)
     D = h.layout[0]["D"]
@@ -65,6 +66,10 @@ def test_power_spectrum_of_prescribed_series_matches_numpy():
         psd, freq, nw = nd.nd_power_spectrum(h.h, 2, comp, window, dt)
         assert nw == n // window
         for r in range(2):
+            # the recorded series (FP32 states averaged in FP64) is the input of both
+            orc, nwo = O.power_spectrum(got[r, :, comp], window, dt)
+            assert nwo == nw
+            assert np.max(np.abs(psd[r] - orc)) <= 1e-10 * orc.max()
             ref, fref = numpy_psd(series[r, :, comp], window, dt)
             assert np.allclose(freq, fref, rtol=1e-14)
             assert np.max(np.abs(psd[r] - ref)) <= 1e-6 * ref.max()

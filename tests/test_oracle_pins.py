@@ -694,3 +694,90 @@ def test_set_green_scaling_zz_halves_the_perpendicular_demag(O):
     h2 = model.demag(m)
     assert np.array_equal(h2[:2], hM[:2])
     assert np.array_equal(h2[2], 0.5 * hM[2])
+
+
+# ------------------------------------------ variants: mask and field pulses
+
+def _shapes(D):
+    """Cell sets of the D x D grid: the full square, an ellipse, an annulus."""
+    idx = np.arange(D) - 0.5 * (D - 1)
+    x, y = np.meshgrid(idx, idx, indexing="xy")
+    r = 0.5 * D
+    return {"square": np.ones((D, D), np.uint8),
+            "ellipse": ((x / r) ** 2 + (y / (0.55 * r)) ** 2 <= 1).astype(np.uint8),
+            "annulus": ((x * x + y * y <= r * r) & (x * x + y * y >= (0.4 * r) ** 2)).astype(np.uint8)}
+
+
+def test_set_mask_with_the_disk_mask_changes_nothing(O):
+    model = O.Model(14e-9, 5e-9, hext=(0, 2e4, 0))
+    m = ndsynth.random_unit_vectors(model.D, seed=3) * model.mask
+    b0, E0, C0 = model.field(m), model.energy(m), model.C
+    model.set_mask(model.mask.copy())
+    assert model.C == C0
+    assert np.array_equal(model.field(m), b0) and model.energy(m) == E0
+
+
+@pytest.mark.parametrize("shape", ["square", "ellipse", "annulus"])
+def test_masked_direct_sum_equals_fft_convolution(O, shape):
+    """Any cell set: the direct sum over the new mask equals the independent
+    FFT convolution restricted to it, the exchange counts neighbours inside it
+    only, and the energy gradient is still -b (Eq. Hmm, Eq. Bi)."""
+    model = O.Model(13e-9, 4e-9)
+    mk = _shapes(model.D)[shape]
+    model.set_mask(mk)
+    assert model.C == int(mk.sum()) and np.array_equal(model.mask, mk)
+    m = ndsynth.random_unit_vectors(model.D, seed=17) * mk
+    ref = fft_convolution_field(O, model, m)
+    hM = model.demag(m)
+    assert np.linalg.norm(hM - ref) <= 1e-12 * np.linalg.norm(ref)
+    u = np.zeros((3, model.D, model.D)); u[0] = mk
+    ex, _ = model.field_parts(u)
+    pad = np.pad(mk, 1).astype(int)
+    nb = pad[:-2, 1:-1] + pad[2:, 1:-1] + pad[1:-1, :-2] + pad[1:-1, 2:]
+    assert np.array_equal(ex[0], nb * mk)
+    # dE/dm_i = -b_i: central difference of the quadratic energy at one cell
+    j, i = np.argwhere(mk)[len(np.argwhere(mk)) // 3]
+    b = model.field(m)
+    for c in range(3):
+        e = np.zeros_like(m); e[c, j, i] = 1e-3
+        g = (model.energy(m + e) - model.energy(m - e)) / 2e-3
+        assert g == pytest.approx(-b[c, j, i], rel=1e-9, abs=1e-12)
+
+
+def test_field_schedule_of_the_static_value_changes_nothing(O):
+    model = O.Model(10e-9, 5e-9, alpha=0.05, hext=(1e4, 0, -2e4))
+    m0 = model.init_vortex(1e-9, 0.0)
+    dtau = 0.02
+    r0, h0 = model.rk4(m0, 7, dtau), model.heun(m0, 7, dtau, 0.01, 3, 5)
+    model.set_schedule(np.tile([1e4, 0, -2e4], (20, 1)))
+    assert np.array_equal(model.rk4(m0, 7, dtau), r0)
+    assert np.array_equal(model.heun(m0, 7, dtau, 0.01, 3, 5), h0)
+    model.set_schedule(None)
+    assert np.array_equal(model.rk4(m0, 7, dtau), r0)
+
+
+def test_field_pulse_precesses_a_macrospin_by_the_closed_form_angle(O):
+    """One cell (D = 1), alpha = 0, field along z: m_z is conserved and the
+    in-plane angle turns at d(phi)/d(tau) = -(a^2/lambda^2)(h_z + (N_x - N_z) m_z)
+    (m x b with the cell's self field -N m).  A pulse h1 for n1 steps, then
+    h0, turns it by the sum of the two rates times their durations; RK4 with
+    the schedule reproduces that to its own accuracy."""
+    a = 2e-9
+    model = O.Model(0.5 * a, 5e-9, a=a, hext=(0, 0, 3e4))
+    assert model.D == 1 and model.C == 1
+    Ms = model.Ms
+    th = 0.7
+    m0 = np.array([np.sin(th), 0.0, np.cos(th)]).reshape(3, 1, 1)
+    n1, n2, dtau, H1 = 300, 500, 0.01, 9e4
+    hs = np.zeros((n1, 3)); hs[:, 2] = H1
+    model.set_schedule(hs)
+    out = model.rk4(m0, n1 + n2, dtau)
+    c, mz = model.c, np.cos(th)
+    rate = lambda H: -c * (H / Ms + (model.Nx - model.Nz) * mz)
+    phi = rate(H1) * n1 * dtau + rate(3e4) * n2 * dtau
+    assert out[2, 0, 0] == pytest.approx(mz, abs=1e-12)
+    got = math.atan2(out[1, 0, 0], out[0, 0, 0])
+    assert abs((got - phi + math.pi) % (2 * math.pi) - math.pi) < 1e-9
+    # the same run split in two calls, the second starting at step n1 + 100
+    mid = model.rk4(m0, n1 + 100, dtau, step0=0)
+    assert np.allclose(model.rk4(mid, n2 - 100, dtau, step0=n1 + 100), out, atol=1e-14)
