@@ -210,6 +210,24 @@ int nd_step_heun(nd_handle *h, void *m, long long n_steps, double dt_seconds, co
 int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int max_iter, double *U_out,
                          double *lambda_out, int *iters_out, void *stream);
 
+/* One sweep of the constrained relaxation of nd_relax_constrained (same
+ * constraint, window, damping eta = 1/2 and Newton step) whose effective field
+ * is taken from an energy gradient the caller supplies, instead of being
+ * evaluated by the library: b_i = -(1/J) grad_i, grad = dE/dm in joules in the
+ * state layout of the handle's precision (for instance the backward of an
+ * autograd energy, which may add terms of its own to the energy of Eq. Hmm).
+ * With grad = -J b this is exactly the library's own sweep.  Per replica:
+ * the residual max |m x e|/|e| of the current state is written to resid_out
+ * (host [B], may be NULL); if it is below tol the replica is left unchanged
+ * (moved_out[r] = 0), otherwise one Newton step on the multipliers lambda
+ * (host [B][2], in/out; start from zero) and the damped alignment update m in
+ * place (moved_out[r] = 1; moved_out may be NULL).  X: host [B][2] core
+ * positions in metres.  m and grad must be device buffers.  Synchronises
+ * `stream`.  The paper has no counterpart (its relaxation is the alignment of
+ * Sec. IV with the library's own field). */
+int nd_relax_sweep_grad(nd_handle *h, void *m, const void *grad, const double *X, double *lambda, double tol,
+                        double *resid_out, int *moved_out, void *stream);
+
 /* Synchronise `stream` and read (then clear) the handle's device status
  * word.  Returns ND_ERR_TIMEOUT if a bounded device-side wait expired since
  * the last check (the time-sliced stepping schedule hands replicas between

@@ -62,6 +62,7 @@ SIGNATURES = {
     "nd_vortex_core": (_I, [_P, _P, _P, _P, _P]),
     "nd_mean_m": (_I, [_P, _P, _P, _P]),
     "nd_relax_constrained": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P]),
+    "nd_relax_sweep_grad": (_I, [_P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "nd_stats_reset": (_I, [_P, _D, _I, _D, _I]),
     "nd_check_status": (_I, [_P, _P]),
     "nd_selftest_handover_timeout": (_I, [_P, _P]),
@@ -237,6 +238,18 @@ def nd_relax_constrained(h, m, X, nrep, tol=1e-6, max_iter=20000, stream=None, c
 def nd_init_vortex(h, m, X0, stream=None):
     X = np.ascontiguousarray(X0, dtype=np.float64)
     _check(lib().nd_init_vortex(h, _ptr(m), _ptr(X), _stream(stream)))
+
+
+def nd_relax_sweep_grad(h, m, grad, X, lam, nrep, tol=0.0, stream=None):
+    """One gradient-driven relaxation sweep; lam ([nrep, 2] float64) is updated
+    in place.  Returns (resid [nrep], moved [nrep] bool)."""
+    Xa = np.ascontiguousarray(X, dtype=np.float64).reshape(nrep, 2)
+    assert lam.dtype == np.float64 and lam.flags["C_CONTIGUOUS"] and lam.shape == (nrep, 2)
+    res = np.zeros(nrep)
+    moved = np.zeros(nrep, dtype=np.int32)
+    _check(lib().nd_relax_sweep_grad(h, _ptr(m), _ptr(grad), _ptr(Xa), _ptr(lam), tol, _ptr(res), _ptr(moved),
+                                     _stream(stream)))
+    return res, moved.astype(bool)
 
 
 def nd_vortex_core(h, m, nrep, stream=None, check=False):

@@ -866,6 +866,62 @@ int nd_relax_constrained(nd_handle *h, void *m, const double *X, double tol, int
     return rc;
 }
 
+int nd_relax_sweep_grad(nd_handle *h, void *m, const void *grad, const double *X, double *lambda, double tol,
+                        double *resid_out, int *moved_out, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!m || !grad || !X || !lambda) return fail(ND_ERR_ARG, "null argument");
+    if (!is_device_ptr(m) || !is_device_ptr(grad)) return fail(ND_ERR_ARG, "m and grad must be device buffers");
+    if (!(tol >= 0)) return fail(ND_ERR_ARG, "tol must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = (int)h->rep_disk.size();
+    if (int rc = ensure_alloc((void **)&h->relax_part, sizeof(double) * 6 * kRelaxBlocks * (size_t)B)) return rc;
+    ND_CUDA(cudaStreamSynchronize(st));   // the pinned relaxation block and aux_d are rewritten below
+    std::vector<double> gs(B);
+    for (int r = 0; r < B; ++r) {
+        const DiskInfo &d = h->disks[h->rep_disk[r]];
+        RelaxIO &R = h->rio_h[r];
+        R.X[0] = X[2 * r] / d.desc.a;
+        R.X[1] = X[2 * r + 1] / d.desc.a;
+        R.lam[0] = lambda[2 * r];
+        R.lam[1] = lambda[2 * r + 1];
+        R.resid = 0.0;
+        R.iters = 0;
+        R.status = 1;
+        gs[r] = -1.0 / d.J;
+    }
+    ND_CUDA(cudaMemcpyAsync(h->rio_d, h->rio_h, sizeof(RelaxIO) * B, cudaMemcpyHostToDevice, st));
+    ND_CUDA(cudaMemcpyAsync(h->aux_d, gs.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    fill_reps(h, h->prec == ND_FP64, 0.0, nullptr, nullptr, 0);
+    upload_reps(h, st);
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    for (auto &c : h->classes) {
+        const DiskInfo &d = h->disks[h->rep_disk[c.reps[0]]];
+        const double rcut = 4.0 * d.lambda / d.desc.a;
+        LaunchArgs a;
+        a.reps = h->reps_d;
+        a.work = c.work_d;
+        a.nwork = (int)c.reps.size();
+        a.y = m;
+        a.stream = st;
+        a.rio = h->rio_d;
+        a.part = h->relax_part;
+        a.eta = 0.5;
+        a.tol = tol;
+        a.rc2 = rcut * rcut;
+        ND_CUDA(launch_relax_grad(prec, a, c.maxD, grad, h->aux_d));
+    }
+    ND_CUDA(cudaMemcpyAsync(h->rio_h, h->rio_d, sizeof(RelaxIO) * B, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < B; ++r) {
+        lambda[2 * r] = h->rio_h[r].lam[0];
+        lambda[2 * r + 1] = h->rio_h[r].lam[1];
+        if (resid_out) resid_out[r] = h->rio_h[r].resid;
+        if (moved_out) moved_out[r] = h->rio_h[r].status != 0;
+    }
+    return ND_OK;
+}
+
 int nd_init_vortex(nd_handle *h, void *m, const double *X0, void *stream)
 {
     if (int rc = check_handle(h)) return rc;

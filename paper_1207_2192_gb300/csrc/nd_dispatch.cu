@@ -17,6 +17,8 @@ cudaError_t launch_fused_f32(int P, const LaunchArgs &a);
 cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
 cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
 cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD);
+cudaError_t launch_relax_grad_f32(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
+cudaError_t launch_relax_grad_f64(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im)
 {
@@ -49,6 +51,11 @@ cudaError_t launch_fused(int P, int prec, const LaunchArgs &a)
 cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD)
 {
     return prec == ND_PREC_FP64 ? launch_global_f64(P, a, maxD) : launch_global_f32(P, a, maxD);
+}
+
+cudaError_t launch_relax_grad(int prec, const LaunchArgs &a, int maxD, const void *grad, const double *gscale)
+{
+    return prec == ND_PREC_FP64 ? launch_relax_grad_f64(a, maxD, grad, gscale) : launch_relax_grad_f32(a, maxD, grad, gscale);
 }
 
 size_t spec_words(int P, int D)

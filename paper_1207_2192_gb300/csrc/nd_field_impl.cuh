@@ -952,6 +952,87 @@ __global__ void __launch_bounds__(256)
     ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < (T)rc2_d, dx, dy, m0, m1, (T)eta_d, dummy));
 }
 
+// The same sweep driven by an externally computed energy gradient: the field
+// is b_i = gscale[r] * grad_i with gscale = -1/J (grad = dE/dm in joules, in
+// the state layout), read in place of the spectrum rows.  Used by
+// nd_relax_sweep_grad.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_relax_grad_reduce(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ mbase,
+                        const T *__restrict__ gbase, const double *__restrict__ gscale,
+                        const RelaxIO *__restrict__ rio, double rc2_d, double eta_d, double *__restrict__ part)
+{
+    __shared__ RelaxAcc<T> racc[8];
+    const int ridx = work[blockIdx.y], tid = threadIdx.x;
+    if (rio[ridx].status == 0) return;   // CTA-uniform
+    const Replica &r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const long long ms_s = (long long)D * r.Dpad;
+    const V3Ptr<T> ms{const_cast<T *>(mbase) + r.state_off, ms_s}, gr{const_cast<T *>(gbase) + r.state_off, ms_s};
+    const T relX = (T)rio[ridx].X[0], relY = (T)rio[ridx].X[1], l0 = (T)rio[ridx].lam[0], l1 = (T)rio[ridx].lam[1];
+    const T eta = (T)eta_d, rc2 = (T)rc2_d, sc = (T)gscale[ridx];
+    RelaxAcc<T> a = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int cell = blockIdx.x * 256 + tid; cell < DD; cell += kRelaxBlocks * 256) {
+        if (!r.mask[cell]) continue;
+        const int y = cell / D, x = cell - y * D;
+        const long long si = (long long)y * r.Dpad + x;
+        const vec3<T> g = gr.ld(si), b = {sc * g.x, sc * g.y, sc * g.z};
+        const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+        relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < rc2, dx, dy, l0, l1, eta, a);
+    }
+    a.C0 = warp_sum_t(a.C0); a.C1 = warp_sum_t(a.C1); a.J00 = warp_sum_t(a.J00);
+    a.J01 = warp_sum_t(a.J01); a.J11 = warp_sum_t(a.J11); a.res = warp_max_t(a.res);
+    if ((tid & 31) == 0) racc[tid >> 5] = a;
+    __syncthreads();
+    if (tid == 0) {
+        RelaxAcc<T> t = racc[0];
+        for (int w = 1; w < 8; ++w) {
+            t.C0 += racc[w].C0; t.C1 += racc[w].C1; t.J00 += racc[w].J00; t.J01 += racc[w].J01;
+            t.J11 += racc[w].J11; t.res = max(t.res, racc[w].res);
+        }
+        double *o = part + ((size_t)ridx * kRelaxBlocks + blockIdx.x) * 6;
+        o[0] = t.C0; o[1] = t.C1; o[2] = t.J00; o[3] = t.J01; o[4] = t.J11; o[5] = t.res;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_relax_grad_update(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ mbase,
+                        const T *__restrict__ gbase, const double *__restrict__ gscale,
+                        const RelaxIO *__restrict__ rio, double rc2_d, double eta_d)
+{
+    const int ridx = work[blockIdx.y];
+    if (rio[ridx].status == 0) return;
+    const Replica &r = reps[ridx];
+    const int D = r.D, DD = D * D;
+    const int cell = blockIdx.x * 256 + threadIdx.x;
+    if (cell >= DD || !r.mask[cell]) return;
+    const long long ms_s = (long long)D * r.Dpad;
+    V3Ptr<T> ms{mbase + r.state_off, ms_s};
+    const V3Ptr<T> gr{const_cast<T *>(gbase) + r.state_off, ms_s};
+    const T relX = (T)rio[ridx].X[0], relY = (T)rio[ridx].X[1], m0 = (T)rio[ridx].lam[0], m1 = (T)rio[ridx].lam[1];
+    const T sc = (T)gscale[ridx];
+    const int y = cell / D, x = cell - y * D;
+    const long long si = (long long)y * r.Dpad + x;
+    const vec3<T> g = gr.ld(si), b = {sc * g.x, sc * g.y, sc * g.z};
+    const T dx = (T)x - T(0.5) * (T)(D - 1) - relX, dy = (T)y - T(0.5) * (T)(D - 1) - relY;
+    RelaxAcc<T> dummy = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    ms.st(si, relax_cell<T>(ms.ld(si), b, dx * dx + dy * dy < (T)rc2_d, dx, dy, m0, m1, (T)eta_d, dummy));
+}
+
+// One gradient-driven sweep over the replicas of one size class.
+template <typename T>
+static cudaError_t launch_relax_grad_t(const LaunchArgs &a, int maxD, const void *grad, const double *gscale)
+{
+    const dim3 gp(kRelaxBlocks, a.nwork), gu((maxD * maxD + 255) / 256, a.nwork);
+    k_relax_grad_reduce<T><<<gp, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.y, (const T *)grad, gscale, a.rio,
+                                                     a.rc2, a.eta, a.part);
+    k_g_relax_newton<<<(a.nwork + 127) / 128, 128, 0, a.stream>>>(a.work, a.nwork, a.rio, a.part, a.tol, 0);
+    k_relax_grad_update<T><<<gu, 256, 0, a.stream>>>(a.reps, a.work, (T *)a.y, (const T *)grad, gscale, a.rio, a.rc2,
+                                                     a.eta);
+    return cudaGetLastError();
+}
+
 // The stage buffer back to the caller's state (cells inside the disk).
 template <typename T>
 __global__ void k_g_store_stage(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ msbase,

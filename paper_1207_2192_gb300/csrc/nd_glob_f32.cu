@@ -19,4 +19,9 @@ cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD)
     }
 }
 
+cudaError_t launch_relax_grad_f32(const LaunchArgs &a, int maxD, const void *grad, const double *gscale)
+{
+    return launch_relax_grad_t<float>(a, maxD, grad, gscale);
+}
+
 }  // namespace nd

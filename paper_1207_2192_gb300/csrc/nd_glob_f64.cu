@@ -19,4 +19,9 @@ cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD)
     }
 }
 
+cudaError_t launch_relax_grad_f64(const LaunchArgs &a, int maxD, const void *grad, const double *gscale)
+{
+    return launch_relax_grad_t<double>(a, maxD, grad, gscale);
+}
+
 }  // namespace nd

@@ -65,6 +65,10 @@ int fused_variant_threads(int P, int variant);   // 0 if the variant does not ex
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
 cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD);
 size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] spectrum
+// One constrained-relaxation sweep over a size class with the field taken
+// from an energy gradient: b = gscale[r] * grad (a.y: the state, a.rio/a.part:
+// multipliers and partial sums, a.tol: convergence threshold).
+cudaError_t launch_relax_grad(int prec, const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
 
 // Spectral kernel build (Section II.B tensor, cell self terms, exchange folded in).
 // Gq: optional device table [4][D][D] of a^2 G at displacements (dx, dy) >= 0 (comps xx, yy, xy, zz,
