@@ -15,13 +15,13 @@ from . import _binding as _b
 from ._binding import (ND_METHOD_HEUN, ND_METHOD_RK4, nd_autotune, nd_plan_info, nd_set_plan, nd_graph_create, nd_graph_destroy, nd_graph_launch,
                        nd_graph_nodes, nd_check_status, nd_selftest_handover_timeout, nd_series_reset,
                        nd_series_sample, nd_series_read, nd_power_spectrum, ND_GRAPH_STATS, ND_GRAPH_SERIES, ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NAN, ND_ERR_NO_VORTEX, ND_ERR_NOT_CONVERGED, ND_ERR_TIMEOUT,
-                       ND_FP32, ND_FP64, ND_OK, NDError, nd_create_disk, nd_destroy, nd_disk_desc, nd_disk_mask,
+                       ND_FP32, ND_FP64, ND_GRID_3X, ND_OK, NDError, nd_create_disk, nd_destroy, nd_disk_desc, nd_disk_mask,
                        nd_effective_field, nd_energy, nd_get_info, nd_init_vortex, nd_last_error, nd_mean_m,
                        nd_relax_constrained, nd_replica_layout, nd_set_damping, nd_set_green_tensor, nd_step_heun,
                        nd_set_mask, nd_set_field_schedule,
                        nd_stats_read, nd_stats_reset, nd_stats_sample, nd_step_rk4, nd_units, nd_vortex_core)
 
-__all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "nd_create_disk", "nd_destroy", "nd_effective_field",
+__all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "ND_GRID_3X", "nd_create_disk", "nd_destroy", "nd_effective_field",
            "nd_energy", "nd_step_rk4", "nd_step_heun", "nd_init_vortex", "nd_vortex_core", "nd_mean_m",
            "nd_set_green_tensor", "nd_set_damping", "nd_set_mask", "nd_set_field_schedule", "nd_units", "nd_replica_layout", "nd_get_info",
            "nd_disk_mask", "nd_last_error", "nd_relax_constrained",
@@ -58,11 +58,12 @@ def ctypes_double3(*v):
 class Nanodisk:
     """One library handle: disks, replicas and their state layout."""
 
-    def __init__(self, disks, replicas=None, precision=ND_FP32):
+    def __init__(self, disks, replicas=None, precision=ND_FP32, grid3x=False):
+        """grid3x: allow the padded size 192 (3 x 64) for disks of 65..96 cells."""
         disks = list(disks) if isinstance(disks, (list, tuple)) else [disks]
         self.disks = disks
         self.precision = precision
-        self.h = nd_create_disk([d.desc() for d in disks], replicas, precision)
+        self.h = nd_create_disk([d.desc() for d in disks], replicas, precision | (ND_GRID_3X if grid3x else 0))
         self.B, self.state_elems = nd_get_info(self.h)
         self.layout = [nd_replica_layout(self.h, r) for r in range(self.B)]
         self.rep_disk = []

@@ -17,6 +17,7 @@ from . import build as _build
 
 ND_OK, ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NOT_CONVERGED, ND_ERR_NO_VORTEX, ND_ERR_TIMEOUT, ND_ERR_NAN = range(7)
 ND_FP32, ND_FP64 = 0, 1
+ND_GRID_3X = 0x100
 ND_METHOD_RK4, ND_METHOD_HEUN = 0, 1
 
 _lock = threading.Lock()

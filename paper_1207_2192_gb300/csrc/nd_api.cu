@@ -77,6 +77,15 @@ int next_pow2_at_least(int n)
     return p;
 }
 
+// Padded FFT side for a linear convolution of span n = 2D - 1: the next power
+// of two, or with ND_GRID_3X the 3 * 2^n size 192 where it is smaller.
+int padded_size(int n, bool allow3)
+{
+    const int p2 = next_pow2_at_least(n);
+    if (allow3 && n <= 192 && p2 > 192) return 192;
+    return p2;
+}
+
 bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes at;
@@ -372,7 +381,10 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     if (!out) return fail(ND_ERR_ARG, "out is null");
     *out = nullptr;
     if (!disks || n_disks < 1) return fail(ND_ERR_ARG, "need at least one disk");
-    if (precision != ND_FP32 && precision != ND_FP64) return fail(ND_ERR_ARG, "precision must be ND_FP32 or ND_FP64");
+    const bool allow3 = (precision & ND_GRID_3X) != 0;
+    precision &= ~ND_GRID_3X;
+    if (precision != ND_FP32 && precision != ND_FP64)
+        return fail(ND_ERR_ARG, "precision must be ND_FP32 or ND_FP64 (optionally with ND_GRID_3X)");
     nd_handle *h = new nd_handle();
     h->prec = precision;
     h->elt = precision == ND_FP64 ? 8 : 4;
@@ -399,7 +411,7 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
         di.D = (int)floor(2.0 * ds.R / ds.a + 0.5);
         if (di.D < 1) { nd_destroy(h); return fail(ND_ERR_ARG, "disk smaller than one cell"); }
         di.Dpad = (di.D + 3) / 4 * 4;
-        di.P = next_pow2_at_least(2 * di.D - 1);
+        di.P = padded_size(2 * di.D - 1, allow3);
         if (di.P > 1024) { nd_destroy(h); return fail(ND_ERR_ARG, "disk too large: padded grid above 1024"); }
         di.lambda = sqrt(2.0 * ds.A / (kMu0 * ds.Ms * ds.Ms));
         di.cfac = ds.a * ds.a / (di.lambda * di.lambda);

@@ -83,8 +83,8 @@ __global__ void k_ghat_pass1(int P, int D, const double *Gq, const double *cs, d
         const double *g = Gq + (size_t)c * D * D + (size_t)dy * D;
         const double *fc = cs + (c == 2 ? 1 : 0);
         double acc = g[0] * fc[0];
-        // phase index kx*dx mod P, advanced by kx per term (P is a power of two)
-        for (int dx = 1, k = kx; dx < D; ++dx, k = (k + kx) & (P - 1)) acc += 2.0 * g[dx] * fc[2 * k];
+        // phase index kx*dx mod P, advanced by kx per term
+        for (int dx = 1, k = kx; dx < D; ++dx, k = (k + kx >= P) ? k + kx - P : k + kx) acc += 2.0 * g[dx] * fc[2 * k];
         T1[i] = acc;
     }
 }
@@ -106,7 +106,8 @@ __global__ void k_ghat_pass2(int P, int D, double cfac, const double *T1, const 
             const double *t1 = T1 + (size_t)c * D * KH + kx;
             const double *fc = cs + (c == 2 ? 1 : 0);
             double acc = t1[0] * fc[0];
-            for (int dy = 1, k = ky; dy < D; ++dy, k = (k + ky) & (P - 1)) acc += 2.0 * t1[(size_t)dy * KH] * fc[2 * k];
+            for (int dy = 1, k = ky; dy < D; ++dy, k = (k + ky >= P) ? k + ky - P : k + ky)
+                acc += 2.0 * t1[(size_t)dy * KH] * fc[2 * k];
             v[c] = (c == 2) ? -acc : acc;
         }
         const double kex = with_exchange ? 2.0 * cs[2 * kx] + 2.0 * cs[2 * ky] : 0.0;

@@ -60,9 +60,9 @@ cudaError_t launch_relax_grad(int prec, const LaunchArgs &a, int maxD, const voi
 
 size_t spec_words(int P, int D)
 {
-    const int RS = (P >= 256) ? (P / 2 + 4) : (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);   // matches SpecGeom<P>::RS
+    const int RS = (P > 128) ? (P / 2 + 4) : (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);   // matches SpecGeom<P>::RS
     // rounded to 16 complex words (128 B for FP32) so every replica's spectrum,
-    // and for P >= 256 every row of it, starts on a 32-byte sector
+    // and for P > 128 every row of it, starts on a 32-byte sector
     return ((size_t)3 * D * RS + 15) / 16 * 16;
 }
 

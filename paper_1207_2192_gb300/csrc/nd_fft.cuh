@@ -16,17 +16,25 @@
 
 namespace nd {
 
-// 32nd roots of unity exp(-2 pi i k / 32), k = 0..31, in the constant bank.
-// Each translation unit that includes this header owns a copy, filled by its
-// own upload hook (ND_DEFINE_TWIDDLE_UPLOAD).  Indices are compile-time
-// constants in the register DFTs, so each use becomes a constant-bank operand.
+// 32nd roots of unity exp(-2 pi i k / 32), k = 0..31, and 24th roots
+// exp(-2 pi i k / 24), k = 0..23 (for the stages of transforms with a factor
+// 3), in the constant bank.  Each translation unit that includes this header
+// owns a copy, filled by its own upload hook (ND_DEFINE_TWIDDLE_UPLOAD).
+// Indices are compile-time constants in the register DFTs, so each use becomes
+// a constant-bank operand.
 static __constant__ float2 c_w32f[32];
 static __constant__ double2 c_w32d[32];
+static __constant__ float2 c_w24f[24];
+static __constant__ double2 c_w24d[24];
 
 template <typename T> __device__ __forceinline__ cplx<T> w32(int k);
 template <> __device__ __forceinline__ cplx<float> w32<float>(int k) { float2 v = c_w32f[k]; return {v.x, v.y}; }
 template <> __device__ __forceinline__ cplx<double> w32<double>(int k) { double2 v = c_w32d[k]; return {v.x, v.y}; }
+template <typename T> __device__ __forceinline__ cplx<T> w24(int k);
+template <> __device__ __forceinline__ cplx<float> w24<float>(int k) { float2 v = c_w24f[k]; return {v.x, v.y}; }
+template <> __device__ __forceinline__ cplx<double> w24<double>(int k) { double2 v = c_w24d[k]; return {v.x, v.y}; }
 
+// re/im: the 32 roots exp(-2 pi i k/32); the 24 roots are computed here.
 #define ND_DEFINE_TWIDDLE_UPLOAD(name)                                                  \
     cudaError_t name(const double *re, const double *im)                                \
     {                                                                                   \
@@ -36,9 +44,18 @@ template <> __device__ __forceinline__ cplx<double> w32<double>(int k) { double2
             f[k] = make_float2((float)re[k], (float)im[k]);                             \
             d[k] = make_double2(re[k], im[k]);                                          \
         }                                                                               \
+        float2 f24[24];                                                                 \
+        double2 d24[24];                                                                \
+        for (int k = 0; k < 24; ++k) {                                                  \
+            const double c = cos(2.0 * M_PI * k / 24.0), s = -sin(2.0 * M_PI * k / 24.0); \
+            f24[k] = make_float2((float)c, (float)s);                                   \
+            d24[k] = make_double2(c, s);                                                \
+        }                                                                               \
         cudaError_t e = cudaMemcpyToSymbol(c_w32f, f, sizeof(f));                        \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32d, d, sizeof(d));             \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w24f, f24, sizeof(f24));         \
         if (e != cudaSuccess) return e;                                                 \
-        return cudaMemcpyToSymbol(c_w32d, d, sizeof(d));                                \
+        return cudaMemcpyToSymbol(c_w24d, d24, sizeof(d24));                            \
     }
 
 template <int P> struct FFTShape;
@@ -49,6 +66,9 @@ template <> struct FFTShape<128> { static constexpr int G = 8; };
 template <> struct FFTShape<256> { static constexpr int G = 16; };
 template <> struct FFTShape<512> { static constexpr int G = 16; };
 template <> struct FFTShape<1024> { static constexpr int G = 32; };
+// 192 = 8 x 24 (a radix-3 stage in the 24-point register DFT): the smallest
+// grid of the form 2^n or 3 * 2^n above 128 for disks of 65..96 cells
+template <> struct FFTShape<192> { static constexpr int G = 8; };
 
 template <int P> struct FFTGeom {
     static constexpr int G = FFTShape<P>::G;
@@ -71,44 +91,78 @@ __host__ __device__ constexpr int bitrev(int i, int bits)
     return r;
 }
 
-// b * w^k for the N-th root w = exp(DIR 2 pi i / N) (DIR = -1 forward), with
-// the trivial factors 1 and -+i special-cased; k and N are constants after the
-// register DFT loops are unrolled, so the branches fold away.
+// b * w^k for the N-th root w = exp(DIR 2 pi i / N) (DIR = -1 forward), N a
+// power of two up to 32 or a divisor of 24, with the trivial factors 1, -1
+// and -+i special-cased; k and N are constants after the register DFT loops
+// are unrolled, so the branches fold away.
 template <int DIR, typename T>
 __device__ __forceinline__ cplx<T> twid(cplx<T> b, int k, int N)
 {
+    k %= N;
     if (k == 0) return b;
+    if (2 * k == N) return cplx<T>{-b.x, -b.y};
     if (4 * k == N) {  // exp(DIR i pi / 2) = DIR * i
         return DIR < 0 ? cplx<T>{b.y, -b.x} : cplx<T>{-b.y, b.x};
     }
-    cplx<T> w = w32<T>(k * (32 / N));
+    if (4 * k == 3 * N) return DIR < 0 ? cplx<T>{-b.y, b.x} : cplx<T>{b.y, -b.x};
+    cplx<T> w = (32 % N == 0) ? w32<T>(k * (32 / N)) : w24<T>(k * (24 / N));
     return DIR < 0 ? cmul(b, w) : cmulc(b, w);
 }
 
-// In-register N-point DFT (N = 2..32), natural order in and out:
-// v[k] <- sum_n v[n] exp(DIR 2 pi i n k / N).
+// In-register N-point DFT, natural order in and out:
+// v[k] <- sum_n v[n] exp(DIR 2 pi i n k / N), for N a power of two up to 32
+// (radix 2) or three times one (one radix-3 stage on top, N | 24).
 template <int N, int DIR, typename T>
 __device__ __forceinline__ void dft_reg(cplx<T> *v)
 {
-    constexpr int B = ilog2c(N);
-    cplx<T> u[N];
+    if constexpr ((N & (N - 1)) == 0) {
+        constexpr int B = ilog2c(N);
+        cplx<T> u[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) u[bitrev(i, B)] = v[i];
+        for (int i = 0; i < N; ++i) u[bitrev(i, B)] = v[i];
 #pragma unroll
-    for (int half = 1; half < N; half *= 2) {
+        for (int half = 1; half < N; half *= 2) {
 #pragma unroll
-        for (int g = 0; g < N; g += 2 * half) {
+            for (int g = 0; g < N; g += 2 * half) {
 #pragma unroll
-            for (int j = 0; j < half; ++j) {
-                cplx<T> a = u[g + j];
-                cplx<T> b = twid<DIR>(u[g + j + half], j, 2 * half);
-                u[g + j] = cadd(a, b);
-                u[g + j + half] = csub(a, b);
+                for (int j = 0; j < half; ++j) {
+                    cplx<T> a = u[g + j];
+                    cplx<T> b = twid<DIR>(u[g + j + half], j, 2 * half);
+                    u[g + j] = cadd(a, b);
+                    u[g + j + half] = csub(a, b);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = u[i];
+        for (int i = 0; i < N; ++i) v[i] = u[i];
+    } else {
+        static_assert(N % 3 == 0 && 24 % N == 0, "register DFT sizes: 2^n <= 32 or divisors of 24");
+        // decimation in time by 3: three N/3-point DFTs of the residues n = 3m + r,
+        // then N/3 three-point butterflies with the twiddles w_N^{rk}
+        constexpr int M = N / 3;
+        cplx<T> a[M], b[M], c[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            a[m] = v[3 * m];
+            b[m] = v[3 * m + 1];
+            c[m] = v[3 * m + 2];
+        }
+        dft_reg<M, DIR>(a);
+        dft_reg<M, DIR>(b);
+        dft_reg<M, DIR>(c);
+        const T h3 = T(0.86602540378443864676);   // sin(pi/3)
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const cplx<T> bk = twid<DIR>(b[k], k, N), ck = twid<DIR>(c[k], 2 * k, N);
+            const cplx<T> s = cadd(bk, ck), d = csub(bk, ck);
+            const cplx<T> t = {a[k].x - T(0.5) * s.x, a[k].y - T(0.5) * s.y};
+            // exp(DIR 2 pi i/3) = -1/2 + DIR i sin(pi/3): X[k + M] = t + DIR i h3 d, X[k + 2M] = t - DIR i h3 d
+            const cplx<T> e = DIR < 0 ? cplx<T>{h3 * d.y, -h3 * d.x} : cplx<T>{-h3 * d.y, h3 * d.x};
+            v[k] = cadd(a[k], s);
+            v[k + M] = cadd(t, e);
+            v[k + 2 * M] = csub(t, e);
+        }
+    }
 }
 
 // N-point DFT of an input whose upper half is zero (v[j] = 0 for j >= N/2):

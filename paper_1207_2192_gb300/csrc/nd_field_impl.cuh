@@ -1063,9 +1063,9 @@ inline int fused_nt(int P, int variant)
     }
 }
 template <int P> struct GlobNT { static constexpr int v = 256; };
-// The tiled column pass runs from P = 256 up (rows of the global spectrum
-// start on 32-byte sectors there).
-template <int P> struct GlobTiled { static constexpr bool v = P >= 256; };
+// The tiled column pass runs above P = 128 (rows of the global spectrum start
+// on 32-byte sectors there).
+template <int P> struct GlobTiled { static constexpr bool v = P > 128; };
 
 template <int P, typename T, int NT>
 constexpr size_t glob_smem_bytes()

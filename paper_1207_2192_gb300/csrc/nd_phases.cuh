@@ -23,9 +23,9 @@ namespace nd {
 
 template <int P> struct SpecGeom {
     // on chip (P <= 128) the two padding words keep the column reads free of
-    // bank conflicts; in global memory (P >= 256) four start each row on a
+    // bank conflicts; in global memory (P > 128) four start each row on a
     // 32-byte sector, so the row passes move whole sectors
-    static constexpr int RS = (P >= 256) ? (P / 2 + 4) : (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);
+    static constexpr int RS = (P > 128) ? (P / 2 + 4) : (P >= 32) ? (P / 2 + 2) : (P / 2 + 2 + 8);
     static constexpr int KH = P / 2 + 1;   // kernel table side
 };
 
@@ -58,7 +58,7 @@ __device__ __forceinline__ void mirror_put(const cplx<T> *v, cplx<T> *scr, int t
 template <int P, typename T>
 __device__ __forceinline__ cplx<T> mirror_get(const cplx<T> *scr, int k)
 {
-    return scr[(P - k) & (P - 1)];
+    return scr[k == 0 ? 0 : P - k];
 }
 
 // Number of row tasks: D complex xy rows plus ceil(D/2) z row pairs.
