@@ -178,3 +178,52 @@ def test_equilibrium_radius_and_speed_statistics():
     vdev = np.abs(vcounts[keep] - vexp[keep]).sum() / vexp[keep].sum()
     print(f"V (over 4D) histogram mean |obs - exp| / exp = {vdev:.3f}")
     assert vdev < 0.15
+
+
+def test_config2_force_constant_map_and_damped_gyration():
+    """Config 2: R = 60 nm, L = 10 nm.  Sixteen constrained relaxations at
+    X = 0, 2, ..., 30 nm along x in one batch (Eq. Ux): U(X) rises
+    monotonically, a parabola through the points X <= 10 nm gives k_F within
+    a few per cent of the two-point value at 2a, and the parabola over all
+    sixteen points stays within 3% of it (harmonic to half the radius).  Then RK4
+    at alpha = 0.01 from the vortex relaxed at X = 4 nm: the core spirals in
+    clockwise (p = +1) at the gyration frequency that Eq. OG gives from that
+    k_F, to the accuracy the constraint reading allows."""
+    R, L, a, A = 60e-9, 10e-9, 2e-9, 1.3e-11
+    xs = np.arange(16) * 2e-9
+    h = Nanodisk([Disk(R, L)], [16], nd.ND_FP32)
+    res = kF_map(h, xs, tol=1e-6, max_iter=60000)
+    assert res["converged"]
+    UJ = res["U_J"]
+    assert np.all(np.diff(UJ) > 0)
+    small = xs <= 10e-9
+    xn = xs[small] / 1e-9
+    coef = np.polyfit(0.5 * xn ** 2, UJ[small], 1)
+    kF_small = coef[0] / 1e-18
+    print(f"config 2: kF two-point {res['kF_2pt']:.4e}, parabola X<=10 nm {kF_small:.4e}, "
+          f"all 16 points {res['kF_fit']:.4e} N/m")
+    assert kF_small == pytest.approx(res["kF_2pt"], rel=0.05)
+    # the map stays close to harmonic out to half the radius
+    assert res["kF_fit"] == pytest.approx(kF_small, rel=0.03)
+    hd = Nanodisk([Disk(R, L, alpha=0.01)], [1], nd.ND_FP32)
+    m = hd.empty_device()
+    hd.init_vortex(m, [[4e-9, 0.0]])
+    rc, *_ = hd.relax(m, [[4e-9, 0.0]], tol=1e-6, max_iter=60000)
+    assert rc == nd.ND_OK
+    dtau, chunk = 0.04, 250
+    dt = dtau * hd.units[0][3]
+    om_st = omega_thiele(kF_small, a, L, A)
+    n = int(1.5 * 2 * math.pi / abs(om_st) / (chunk * dtau)) + 1
+    xc, yc = [], []
+    for _ in range(n):
+        hd.rk4(m, chunk, dt)
+        Xc, st = hd.vortex_core(m)
+        assert st[0] == 0
+        xc.append(Xc[0, 0]); yc.append(Xc[0, 1])
+    om = omega_from_core(xc, yc, chunk * dtau)
+    r = np.hypot(xc, yc)
+    print(f"config 2 dynamics: Omega {om:.4e}, Thiele {om_st:.4e} (ratio {om / om_st:.3f}), "
+          f"radius {r[0]*1e9:.2f} -> {r[-1]*1e9:.2f} nm")
+    assert om < 0                                   # clockwise for p = +1
+    assert 1.0 <= om / om_st <= 1.15
+    assert r[-1] < r[0]                             # damping: the core spirals in
