@@ -374,8 +374,9 @@ void nd_graph_destroy(nd_graph *g);
  * The call performs the same n_steps stochastic Heun steps as nd_step_heun on
  * a handle holding n_replicas replicas of *disk in ND_FP32 (same state layout:
  * replica r at element offset r * 3 * D * Dpad), with the same noise stream.
- * Its working memory -- the stage accumulator, the spectral kernel, the mask,
- * the twiddles and the parameter blocks -- lives in one file-scope device
+ * Its working memory -- the stage accumulator, the spectral kernel, the mask
+ * and its cell list, the twiddles and the parameter blocks -- lives in one
+ * file-scope device
  * array of fixed size that every GPU loading the library holds until exit
  * (about 9 MiB); nothing is allocated.  Limits, rejected with ND_ERR_ARG and
  * a message: padded grid P <= 128 (disk diameter up to 64 cells, and the

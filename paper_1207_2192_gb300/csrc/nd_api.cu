@@ -42,6 +42,7 @@ struct DiskInfo {
     double h[3] = {0, 0, 0};   // H_ext / Ms
     std::vector<unsigned char> mask;
     unsigned char *mask_d = nullptr;
+    int *cells_d = nullptr;    // the cells inside the disk (increasing j*D+i), C of them
     double *ghat64 = nullptr;  // [P/2+1][P/2+1][4]
     float *ghat32 = nullptr;
     double *ghatL = nullptr;   // thickness derivative of the demagnetisation kernel (FP64)
@@ -51,6 +52,18 @@ struct DiskInfo {
     double *sched64 = nullptr;
     long long nsched = 0;
 };
+
+// Upload a disk's mask and its compacted cell list (the mask may change).
+static cudaError_t upload_mask(DiskInfo &d)
+{
+    std::vector<int> cells;
+    for (size_t i = 0; i < d.mask.size(); ++i)
+        if (d.mask[i]) cells.push_back((int)i);
+    cudaError_t e = cudaMemcpy(d.mask_d, d.mask.data(), d.mask.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !cells.empty())
+        e = cudaMemcpy(d.cells_d, cells.data(), sizeof(int) * cells.size(), cudaMemcpyHostToDevice);
+    return e;
+}
 
 struct SizeClass {
     int P = 0, maxD = 0, maxDpad = 0;
@@ -199,6 +212,8 @@ static void fill_reps(nd_handle *h, bool fp64_kernel, double dt_seconds, const d
         R.spec_off = h->rep_spec_off[r];
         R.Ghat = table == TAB_DL ? (const void *)d.ghatL : (fp64_kernel ? (const void *)d.ghat64 : (const void *)d.ghat32);
         R.mask = d.mask_d;
+        R.cells = d.cells_d;
+        R.ncells = d.C;
         for (int k = 0; k < 3; ++k) R.chext[k] = table == TAB_DL ? 0.0 : d.cfac * d.h[k];
         R.alpha = h->alpha[r];
         R.dtau = d.desc.gamma * d.B0 * dt_seconds;
@@ -538,7 +553,8 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
         DiskInfo &di = h->disks[d];
         const size_t kh = ghat_table_entries(di.P);
         if ((e = cudaMalloc(&di.mask_d, di.mask.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-        cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice);
+        if ((e = cudaMalloc(&di.cells_d, sizeof(int) * di.mask.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if ((e = upload_mask(di)) != cudaSuccess) return cuda_fail(e, "mask upload");
         if ((e = cudaMalloc(&di.ghat64, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         if ((e = cudaMalloc(&di.ghat32, sizeof(float) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         if ((e = cudaMalloc(&di.ghatL, sizeof(double) * kh)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -556,7 +572,7 @@ void nd_destroy(nd_handle *h)
 {
     if (!h) return;
     for (auto &d : h->disks) {
-        cudaFree(d.mask_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL);
+        cudaFree(d.mask_d); cudaFree(d.cells_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL);
         cudaFree(d.sched32); cudaFree(d.sched64);
     }
     for (auto &c : h->classes) { cudaFree(c.work_d); cudaFree(c.segs_d); cudaFree(c.seg_off_d); }
@@ -669,7 +685,8 @@ int nd_set_mask(nd_handle *h, int d, const unsigned char *mask)
         C += di.mask[i];
     }
     di.C = C;
-    ND_CUDA(cudaMemcpy(di.mask_d, di.mask.data(), di.mask.size(), cudaMemcpyHostToDevice));
+    ND_CUDA(cudaDeviceSynchronize());   // kernels in flight may still read the old cell list
+    ND_CUDA(upload_mask(di));
     return ND_OK;
 }
 

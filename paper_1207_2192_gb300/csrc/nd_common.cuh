@@ -96,6 +96,8 @@ struct Replica {
     const void *Ghat;            // [P/2+1 (kx)][P/2+1 (ky)][4] spectral kernel, incl. exchange and 1/P^2,
                                  // then the same values as [4][P/2+1][P/2+1]
     const unsigned char *mask;   // [D][D]
+    const int *cells;            // the cells inside the disk, j*D+i in increasing order (ncells of them)
+    int ncells, pad_cells;
     double chext[3];             // (a^2/lambda^2) h_ext
     double alpha, dtau, sigma;   // damping, dimensionless step, noise amplitude
     unsigned long long seed, step0;

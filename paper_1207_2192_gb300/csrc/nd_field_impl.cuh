@@ -454,8 +454,10 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
                 // the external field of this step (a scheduled one in the stepping modes)
                 const vec3<T> cx = (MODE == M_RK4 || MODE == M_HEUN) ? step_chext<T>(r, sp, step)
                                                                      : vec3<T>{sp.chext[0], sp.chext[1], sp.chext[2]};
-                for (int cell = tid; cell < DD; cell += NT) {
-                    if (!r.mask[cell]) continue;
+                // over the disk's cells only (a compacted list), so that no warp
+                // spends an iteration on cells outside the disk
+                for (int k = tid; k < r.ncells; k += NT) {
+                    const int cell = __ldg(r.cells + k);
                     const int y = cell / D, x = cell - y * D;
                     const long long si = (long long)y * Dpad + x;
                     const long long hi = (long long)y * (2 * RS) + x;

@@ -12,8 +12,8 @@
 //
 // The array holds, for one FP32 disk geometry with P <= 128: the stage
 // accumulator of the Heun scheme, the spectral kernel (built in place, and
-// rebuilt only when the geometry changes), the disk mask, the FFT twiddles,
-// the per-replica parameter blocks and the work list.  Every call on a device
+// rebuilt only when the geometry changes), the disk mask and its list of
+// cells, the FFT twiddles, the per-replica parameter blocks and the work list.  Every call on a device
 // shares that device's copy and leaves the last call's contents behind;
 // nothing in it has to start at zero (the accumulator is written before it is
 // read), but calls whose kernels overlap on the GPU -- on different streams, or
@@ -46,7 +46,8 @@ constexpr size_t kOffG64 = align256(kOffG32 + sizeof(float) * kGhatEntries);
 constexpr size_t kOffWork = align256(kOffG64 + sizeof(double) * kGhatEntries);
 constexpr size_t kWorkDoubles = (size_t)4 * kMaxD * kMaxD + (size_t)4 * kMaxD * kKH + 2 * (size_t)kMaxP;
 constexpr size_t kOffMask = align256(kOffWork + sizeof(double) * kWorkDoubles);
-constexpr size_t kOffTw = align256(kOffMask + (size_t)kMaxD * kMaxD);
+constexpr size_t kOffCells = align256(kOffMask + (size_t)kMaxD * kMaxD);
+constexpr size_t kOffTw = align256(kOffCells + sizeof(int) * (size_t)kMaxD * kMaxD);
 constexpr size_t kOffReps = align256(kOffTw + sizeof(float) * 2 * kMaxP);
 constexpr size_t kOffList = align256(kOffReps + sizeof(Replica) * kMaxReplicas);
 constexpr size_t kStaticBytes = align256(kOffList + sizeof(int) * kMaxReplicas);
@@ -64,7 +65,7 @@ struct DeviceSlot {
     unsigned char *base = nullptr;   // device address of g_nd_noalloc_scratch on this device
     // geometry whose kernel table, mask and twiddles are currently in the array
     bool have_geom = false;
-    int D = 0, P = 0;
+    int D = 0, P = 0, C = 0;
     double key[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -160,6 +161,7 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
     double *g64 = reinterpret_cast<double *>(S.base + kOffG64);
     double *work = reinterpret_cast<double *>(S.base + kOffWork);
     unsigned char *mask = S.base + kOffMask;
+    int *cells = reinterpret_cast<int *>(S.base + kOffCells);
     float *tw = reinterpret_cast<float *>(S.base + kOffTw);
     Replica *reps = reinterpret_cast<Replica *>(S.base + kOffReps);
     int *list = reinterpret_cast<int *>(S.base + kOffList);
@@ -169,20 +171,24 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
     for (int k = 0; k < 6 && same; ++k) same = S.key[k] == key[k];
     if (!same) {
         unsigned char mh[kMaxD * kMaxD];
+        int ch[kMaxD * kMaxD];
+        int nc = 0;
         const double rr = (ds.R / ds.a) * (ds.R / ds.a);
         for (int j = 0; j < D; ++j)
             for (int i = 0; i < D; ++i) {
                 const double x = i - 0.5 * (D - 1), y = j - 0.5 * (D - 1);
                 mh[j * D + i] = (x * x + y * y) <= rr;
+                if (mh[j * D + i]) ch[nc++] = j * D + i;
             }
         float th[2 * kMaxP];
         for (int k = 0; k < P; ++k) { th[2 * k] = (float)cos(2.0 * M_PI * k / P); th[2 * k + 1] = (float)-sin(2.0 * M_PI * k / P); }
         cudaError_t e = cudaMemcpyAsync(mask, mh, (size_t)D * D, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(cells, ch, sizeof(int) * nc, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tw, th, sizeof(float) * 2 * P, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = build_ghat(P, D, ds.L / ds.a, Nx, Nz, cfac, nullptr, g64, g32, work, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host arrays above are on the stack
         if (e != cudaSuccess) { S.have_geom = false; return fail(ND_ERR_CUDA, std::string("geometry set-up: ") + cudaGetErrorString(e)); }
-        S.have_geom = true; S.D = D; S.P = P;
+        S.have_geom = true; S.D = D; S.P = P; S.C = nc;
         for (int k = 0; k < 6; ++k) S.key[k] = key[k];
     }
     if (n_steps == 0) return ND_OK;
@@ -194,6 +200,7 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
         R.state_off = (long long)r * 3 * D * Dpad;
         R.spec_off = 0;
         R.Ghat = g32; R.mask = mask;
+        R.cells = cells; R.ncells = S.C;
         for (int k = 0; k < 3; ++k) R.chext[k] = cfac * (ds.hext[k] / ds.Ms);   // rounded as nd_create_disk does
         R.alpha = ds.alpha; R.dtau = dtau;
         R.sigma = sqrt(2.0 * ds.alpha * (kB * T_kelvin[r] / J) * dtau);
