@@ -328,18 +328,25 @@ __device__ __forceinline__ void row_inv_fft(cplx<T> *v, bool active, const cplx<
     if constexpr (HALF_LOAD) {
         static_assert(Gm::SCRATCH >= P + 2, "scratch holds both half rows");
         constexpr int KB = P / 2 + 1;   // B's half row starts here in the scratch
+        constexpr int OH = R1 / 2 + 1;  // registers holding k <= P/2
+        // every load first, so that all of them are in flight at once
+        cplx<T> a[OH], b[OH];
 #pragma unroll
-        for (int o = 0; o < R1; ++o) {
+        for (int o = 0; o < OH; ++o) {
+            const int k = t + G * o;
+            a[o] = b[o] = {T(0), T(0)};
+            if (active && k <= P / 2) {
+                a[o] = rA[k];
+                if (hasB) b[o] = rB[k];
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < OH; ++o) {
             const int k = t + G * o;
             if (k <= P / 2) {
-                cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
-                if (active) {
-                    a = rA[k];
-                    if (hasB) b = rB[k];
-                }
-                scr[k] = a;
-                scr[KB + k] = b;
-                v[o] = {a.x - b.y, a.y + b.x};
+                scr[k] = a[o];
+                scr[KB + k] = b[o];
+                v[o] = {a[o].x - b[o].y, a[o].y + b[o].x};
             }
         }
         __syncwarp(gmask);
