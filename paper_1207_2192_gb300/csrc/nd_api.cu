@@ -73,7 +73,7 @@ struct SizeClass {
     bool fused_fp64 = false;   // fused kernel in FP64 (energy)
     size_t smem_main = 0, smem_fp64 = 0;
     size_t smem_wbuf = 0;      // fused Heun with the normals kept in shared memory (0: does not fit)
-    int plan[2] = {-1, -1};    // stepping plan for RK4 / Heun: -1 default, 0..2 fused variant, kPlanGlobal
+    int plan[2] = {-1, -1};    // stepping plan for RK4 / Heun: -1 default, 0..2 fused variant, kPlanGlobal, kPlanCluster
     // time-sliced schedule, cached per (mode, n_steps)
     SegmentHost *segs_d = nullptr;
     int *seg_off_d = nullptr;
@@ -82,6 +82,7 @@ struct SizeClass {
 };
 
 constexpr int kPlanGlobal = 100;
+constexpr int kPlanCluster = 200;   // one replica per thread-block cluster of 8 CTAs (P <= 128)
 
 int next_pow2_at_least(int n)
 {
@@ -286,13 +287,18 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         bool fused = fp64 ? c.fused_fp64 : c.fused_main;
         const bool stepping = (mode == M_HEUN || mode == M_RK4) && !fp64;
         int variant = 0;
+        bool cluster = false;
         if (stepping) {
             const int pl = c.plan[mode == M_RK4 ? 0 : 1];
             if (pl == kPlanGlobal) fused = false;
+            else if (pl == kPlanCluster) cluster = true;
             else if (pl > 0) variant = pl;
         }
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
-        if (fused) {
+        if (cluster) {
+            a.use_wbuf = mode == M_HEUN ? 1 : 0;
+            ND_CUDA(launch_cluster(c.P, prec, a, c.maxD, c.maxDpad));
+        } else if (fused) {
             a.smem = fp64 ? c.smem_fp64 : c.smem_main;
             a.status = h->status_d;
             a.variant = variant;
@@ -1289,6 +1295,10 @@ int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, 
             if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(v);
         }
         cands.push_back(kPlanGlobal);
+        {
+            const size_t sm = cluster_smem(c.P, prec, c.maxD, c.maxDpad, mode == M_HEUN);
+            if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(kPlanCluster);
+        }
         float best_ms = 1e30f;
         int best = cands.front();
         for (int cand : cands) {
@@ -1321,7 +1331,10 @@ int nd_set_plan(nd_handle *h, int cls, int method, int plan)
     if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
     SizeClass &c = h->classes[cls];
     const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
-    if (plan == kPlanGlobal) {
+    if (plan == kPlanCluster) {
+        const size_t sm = cluster_smem(c.P, prec, c.maxD, c.maxDpad, method == ND_METHOD_HEUN);
+        if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return fail(ND_ERR_ARG, "no cluster plan for this size class");
+    } else if (plan == kPlanGlobal) {
         if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
         if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
     } else if (plan >= 0) {
@@ -1329,7 +1342,7 @@ int nd_set_plan(nd_handle *h, int cls, int method, int plan)
         const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, plan);
         if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return fail(ND_ERR_ARG, "variant does not fit in shared memory");
     } else if (plan != -1) {
-        return fail(ND_ERR_ARG, "plan must be -1, 0..2 or 100");
+        return fail(ND_ERR_ARG, "plan must be -1, 0..2, 100 or 200");
     }
     c.plan[method == ND_METHOD_RK4 ? 0 : 1] = plan;
     return ND_OK;
@@ -1343,6 +1356,7 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
     const SizeClass &c = h->classes[cls];
     auto threads = [&](int pl) {
         if (pl == kPlanGlobal) return 0;
+        if (pl == kPlanCluster) return 256 * 8;   // threads of the whole cluster
         if (!c.fused_main) return 0;
         return fused_variant_threads(c.P, pl < 0 ? 0 : pl);
     };

@@ -1,0 +1,282 @@
+// nd_cluster.cuh -- one replica's time steps on a thread-block cluster of NC
+// CTAs (one per SM), for the on-chip sizes P <= 128 when a class has too few
+// replicas to fill the GPU with one CTA each.
+//
+// The replica's rows are split over the cluster: CTA k owns rows
+// [k rpc, (k+1) rpc) of the disk (rpc even, so z row pairs stay whole), and
+// holds those rows of the stage state, of the half spectrum and, afterwards,
+// of the field in its own shared memory.  Per field evaluation (Section II.B
+// convolution):
+//   1. forward rows: each CTA transforms its own rows (no communication);
+//   2. cluster barrier;
+//   3. columns: CTA k takes column slots [k spc, (k+1) spc) of the P/2 slots
+//      (slot 0: the packed real columns kx = 0 and P/2), one FFT group per
+//      (slot, component); a group gathers its column from the owners' shared
+//      memory through distributed shared memory (DSMEM), transforms it,
+//      applies the spectral kernel (the x and y groups of a column exchange
+//      their spectra through local shared memory for the in-plane 2x2 block),
+//      transforms back and scatters the rows to their owners;
+//   4. cluster barrier;
+//   5. inverse rows and the per-cell epilogue (stage_update) on the CTA's own
+//      rows; the next stage's forward rows read only those rows, so a CTA
+//      barrier suffices until the next column pass.
+// The state y_n, the stage accumulator and the Heun predictor's normals of the
+// CTA's rows stay in its shared memory for the whole launch: global memory is
+// read once at the start and written once at the end.
+// The cluster barriers are hardware barriers of co-scheduled CTAs; nothing
+// spins on a flag.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "nd_field_impl.cuh"
+
+namespace nd {
+
+namespace cgc = cooperative_groups;
+
+template <int P, typename T, int NC> struct ClusterGeom {
+    static constexpr int G = FFTGeom<P>::G;
+    static constexpr int NT = 256;
+    static constexpr int NGRP = NT / G;
+    static constexpr int SPC = (P / 2) / NC;   // column slots per CTA
+    static_assert(SPC >= 1 && (P / 2) % NC == 0, "column slots split evenly over the cluster");
+    static_assert(3 * SPC <= NGRP, "one FFT group per (slot, component)");
+};
+
+// Rows per CTA for a grid of D rows: even, so that z row pairs stay in one CTA.
+__host__ __device__ __forceinline__ int cluster_rows(int D, int NC) { return 2 * ((D + 2 * NC - 1) / (2 * NC)); }
+
+template <int P, typename T, int NC>
+__host__ __device__ __forceinline__ size_t cluster_smem_bytes(int D, int Dpad, bool wbuf)
+{
+    using CG = ClusterGeom<P, T, NC>;
+    const int rpc = cluster_rows(D, NC);
+    size_t b = sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G               // twiddles
+                                  + (size_t)3 * rpc * SpecGeom<P>::RS                   // spectrum rows
+                                  + (size_t)CG::NGRP * FFTGeom<P>::SCRATCH);            // FFT scratch
+    b += sizeof(T) * (size_t)3 * rpc * Dpad * (wbuf ? 4 : 3);   // stage state, y_n, accumulator (+ normals)
+    return b;
+}
+
+template <int P, typename T, int MODE, int NC>
+__global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
+    k_cluster(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
+              const cplx<T> *__restrict__ twP, long long nsteps,
+              unsigned long long step_base, int use_wbuf)
+{
+    using Gm = FFTGeom<P>;
+    using CG = ClusterGeom<P, T, NC>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH, NT = CG::NT, NGRP = CG::NGRP;
+    constexpr int SPC = CG::SPC;
+    static_assert(MODE == M_RK4 || MODE == M_HEUN, "stepping modes");
+    cgc::cluster_group cluster = cgc::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    GroupId<P> gid(tid);
+    const int ridx = work[blockIdx.x / NC];
+    const Replica &r = reps[ridx];
+    const int D = r.D, Dpad = r.Dpad, rpc = cluster_rows(D, NC);
+    const int ylo = rank * rpc, nloc = max(0, min(D, ylo + rpc) - ylo);   // this CTA's rows [ylo, ylo + nloc)
+    const long long lcs = (long long)rpc * RS;                            // local spectrum component stride
+    const long long lms = (long long)rpc * Dpad;                          // local state component stride
+    const long long ms_s = (long long)D * Dpad;                           // global state component stride
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
+    cplx<T> *spec = tw + R1 * G;                                          // [3][rpc][RS]
+    cplx<T> *scratch = spec + 3 * lcs;
+    T *msl = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);         // [3][rpc][Dpad]
+    T *ynl = msl + 3 * lms, *accl = ynl + 3 * lms;
+    T *wl = use_wbuf ? accl + 3 * lms : nullptr;
+    cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
+    load_twiddles<P>(tw, twP, tid, NT);
+    const V3Ptr<T> ms{msl, lms}, wb{wl, lms}, ynv{ynl, lms}, accv{accl, lms}, none{nullptr, 0};
+    const V3Ptr<T> yg{ybase + r.state_off, ms_s};
+    // the state of the CTA's rows (zero outside the disk)
+    for (int i = tid; i < nloc * D; i += NT) {
+        const int lr = i / D, x = i - lr * D, y = ylo + lr;
+        const long long si = (long long)y * Dpad + x, mi = (long long)lr * Dpad + x;
+        const vec3<T> m0 = r.mask[y * D + x] ? yg.ldcg(si) : vec3<T>{T(0), T(0), T(0)};
+        ms.st(mi, m0);
+        ynv.st(mi, m0);
+    }
+    // row tasks of this CTA: xy rows 0..nloc-1, then z pairs (0,1), (2,3), ...
+    const int nrt = nloc + (nloc + 1) / 2;
+    // column task of this group: slot j (column kx = rank SPC + j, slot 0 of
+    // rank 0 being the packed pair), component c
+    const int cj = gid.group % SPC, cc = gid.group / SPC;
+    const bool ctask = gid.group < 3 * SPC;   // groups beyond 3 SPC idle in the column pass
+    const int kslot = rank * SPC + cj;
+    const bool packed = ctask && kslot == 0;
+    const T *Ghat = reinterpret_cast<const T *>(r.Ghat);
+    __syncthreads();
+
+    for (long long n = 0; n < nsteps; ++n) {
+        const unsigned long long step = step_base + r.step0 + (unsigned long long)n;
+        for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
+            // 1. forward rows of the CTA's own rows
+            for (int qb = gid.group; qb < ((nrt + NGRP - 1) / NGRP) * NGRP; qb += NGRP) {
+                const int q = qb;
+                const bool act = q < nrt;
+                const bool isxy = q < nloc;
+                const int l0 = isxy ? q : 2 * (q - nloc), l1 = l0 + 1;
+                const bool hasB = isxy || (l1 < nloc);
+                cplx<T> v[R1];
+#pragma unroll
+                for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+                for (int o = 0; o < R1 / 2; ++o) {
+                    const int x = gid.t + G * o;
+                    if (act && x < D) {
+                        if (isxy) v[o] = {msl[(long long)l0 * Dpad + x], msl[lms + (long long)l0 * Dpad + x]};
+                        else v[o] = {msl[2 * lms + (long long)l0 * Dpad + x],
+                                     hasB ? msl[2 * lms + (long long)l1 * Dpad + x] : T(0)};
+                    }
+                }
+                cplx<T> *dA = isxy ? spec + (long long)l0 * RS : spec + 2 * lcs + (long long)l0 * RS;
+                cplx<T> *dB = isxy ? spec + lcs + (long long)l0 * RS : spec + 2 * lcs + (long long)l1 * RS;
+                row_fwd_core<P, T>(v, act, dA, dB, hasB, gid.t, scr, tw, gid.gmask);
+            }
+            cluster.sync();   // every row of every CTA transformed
+            // 3. columns, gathered from and scattered to the owners
+            {
+                cplx<T> v[R1];
+#pragma unroll
+                for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+                const int kx = packed ? 0 : kslot;
+#pragma unroll
+                for (int o = 0; o < R1 / 2; ++o) {
+                    const int y = gid.t + G * o;
+                    if (ctask && y < D) {
+                        const int ow = y / rpc, lr = y - ow * rpc;   // the row's owner
+                        const cplx<T> *src = cluster.map_shared_rank(spec + cc * lcs + (long long)lr * RS, ow);
+                        v[o] = packed ? cplx<T>{src[0].x, src[P / 2].x} : src[kx];
+                    }
+                }
+                if (packed) {
+                    packed_col_fwd_loaded<P, T>(v, cc, Ghat, gid.t, scr, tw, gid.gmask);
+                } else if (ctask) {
+                    fft_group<P, -1, FFT_HALF_IN>(v, gid.t, scr, tw, gid.gmask);
+                }
+                // the x and y groups of a column exchange their spectra
+                if (ctask && !packed && cc < 2) {
+#pragma unroll
+                    for (int o = 0; o < R1; ++o) scr[o * G + gid.t] = v[o];
+                }
+                __syncthreads();
+                if (ctask && !packed) {
+                    constexpr int KK = KH * KH;
+                    const T *Gs = Ghat + 4 * KK + kx * KH;   // component-major copy of the table
+                    if (cc < 2) {
+                        const cplx<T> *other = scratch + ((1 - cc) * SPC + cj) * Gm::SCRATCH;
+                        const T *gd = Gs + cc * KK, *go = Gs + 2 * KK;
+#pragma unroll
+                        for (int o = 0; o < R1; ++o) {
+                            const int ky = gid.t + G * o;
+                            const bool up = ky <= P / 2;
+                            const int kyr = up ? ky : P - ky;
+                            const T gdiag = __ldg(gd + kyr), gxy0 = __ldg(go + kyr);
+                            const T gxy = up ? gxy0 : -gxy0;   // G_xy is odd in ky
+                            const cplx<T> w = other[o * G + gid.t];
+                            v[o] = cc == 0 ? tensor_row(gdiag, v[o], gxy, w) : tensor_row(gxy, w, gdiag, v[o]);
+                        }
+                    } else {
+                        const T *gz = Gs + 3 * KK;
+#pragma unroll
+                        for (int o = 0; o < R1; ++o) {
+                            const int ky = gid.t + G * o;
+                            const int kyr = ky <= P / 2 ? ky : P - ky;
+                            v[o] = cscale(v[o], __ldg(gz + kyr));
+                        }
+                    }
+                }
+                __syncthreads();   // the partners' spectra are read before the scratch is reused
+                if (ctask) fft_group<P, +1, FFT_HALF_OUT>(v, gid.t, scr, tw, gid.gmask);
+#pragma unroll
+                for (int o = 0; o < R1 / 2; ++o) {
+                    const int y = gid.t + G * o;
+                    if (ctask && y < D) {
+                        const int ow = y / rpc, lr = y - ow * rpc;
+                        cplx<T> *dst = cluster.map_shared_rank(spec + cc * lcs + (long long)lr * RS, ow);
+                        if (packed) {
+                            dst[0] = {v[o].x, T(0)};
+                            dst[P / 2] = {v[o].y, T(0)};
+                        } else {
+                            dst[kx] = v[o];
+                        }
+                    }
+                }
+            }
+            cluster.sync();   // every column back with its owner
+            // 5. inverse rows of the CTA's own rows (the field rows, in place)
+            for (int qb = gid.group; qb < ((nrt + NGRP - 1) / NGRP) * NGRP; qb += NGRP) {
+                const int q = qb;
+                const bool act = q < nrt;
+                const bool isxy = q < nloc;
+                const int l0 = isxy ? q : 2 * (q - nloc), l1 = l0 + 1;
+                const bool hasB = isxy || (l1 < nloc);
+                cplx<T> *rA = isxy ? spec + (long long)l0 * RS : spec + 2 * lcs + (long long)l0 * RS;
+                cplx<T> *rB = isxy ? spec + lcs + (long long)l0 * RS : spec + 2 * lcs + (long long)l1 * RS;
+                cplx<T> v[R1];
+                row_inv_fft<P, T>(v, act, rA, rB, hasB, gid.t, scr, tw, gid.gmask);
+                if (act) {
+                    T *oA = reinterpret_cast<T *>(rA), *oB = reinterpret_cast<T *>(rB);
+#pragma unroll
+                    for (int o = 0; o < R1 / 2; ++o) {
+                        const int x = gid.t + G * o;
+                        if (x < D) {
+                            oA[x] = v[o].x;
+                            if (hasB) oB[x] = v[o].y;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // the per-cell epilogue of the CTA's own cells
+            const StepParams<T> sp = step_params<T>(r);
+            const vec3<T> cx = step_chext<T>(r, sp, step);
+            const T *hr = reinterpret_cast<const T *>(spec);
+            for (int i = tid; i < nloc * D; i += NT) {
+                const int lr = i / D, x = i - lr * D, y = ylo + lr, cell = y * D + x;
+                if (!r.mask[cell]) continue;
+                const long long mi = (long long)lr * Dpad + x;
+                const long long hi = (long long)lr * (2 * RS) + x;
+                const vec3<T> b = {hr[hi] + cx.x, hr[2 * lcs + hi] + cx.y, hr[4 * lcs + hi] + cx.z};
+                epilogue_cell<T, MODE>(r, cell, mi, mi, b, ms, ynv, accv, none, stage, step, wb, ynv, accv);
+            }
+            __syncthreads();
+        }
+    }
+    // the final state of the CTA's cells back to the caller's buffer
+    for (int i = tid; i < nloc * D; i += NT) {
+        const int lr = i / D, x = i - lr * D, y = ylo + lr;
+        if (r.mask[y * D + x]) yg.st((long long)y * Dpad + x, ynv.ld((long long)lr * Dpad + x));
+    }
+    cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// The cluster size of the on-chip sizes.
+constexpr int kClusterCTAs = 8;
+
+template <int P, typename T, int MODE>
+static cudaError_t launch_cluster_t(const LaunchArgs &a, int maxD, int maxDpad)
+{
+    constexpr int NC = kClusterCTAs;
+    auto kern = k_cluster<P, T, MODE, NC>;
+    const size_t sm = cluster_smem_bytes<P, T, NC>(maxD, maxDpad, a.use_wbuf != 0);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nwork * NC, ClusterGeom<P, T, NC>::NT, sm, a.stream>>>(a.reps, a.work, (T *)a.y,
+                                                                    (const cplx<T> *)a.tw, a.nsteps, a.step_base,
+                                                                    a.use_wbuf);
+    return cudaGetLastError();
+}
+
+template <int P, typename T>
+static cudaError_t launch_cluster_p(const LaunchArgs &a, int maxD, int maxDpad)
+{
+    if (a.mode == M_RK4) return launch_cluster_t<P, T, M_RK4>(a, maxD, maxDpad);
+    if (a.mode == M_HEUN) return launch_cluster_t<P, T, M_HEUN>(a, maxD, maxDpad);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace nd

@@ -18,6 +18,10 @@ cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
 cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
 cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD);
 cudaError_t launch_relax_grad_f32(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
+size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf);
+size_t cluster_smem_f64(int P, int D, int Dpad, bool wbuf);
+cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad);
+cudaError_t launch_cluster_f64(int P, const LaunchArgs &a, int maxD, int maxDpad);
 cudaError_t launch_relax_grad_f64(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im)
@@ -56,6 +60,16 @@ cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD)
 cudaError_t launch_relax_grad(int prec, const LaunchArgs &a, int maxD, const void *grad, const double *gscale)
 {
     return prec == ND_PREC_FP64 ? launch_relax_grad_f64(a, maxD, grad, gscale) : launch_relax_grad_f32(a, maxD, grad, gscale);
+}
+
+size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf)
+{
+    return prec == ND_PREC_FP64 ? cluster_smem_f64(P, D, Dpad, wbuf) : cluster_smem_f32(P, D, Dpad, wbuf);
+}
+
+cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad)
+{
+    return prec == ND_PREC_FP64 ? launch_cluster_f64(P, a, maxD, maxDpad) : launch_cluster_f32(P, a, maxD, maxDpad);
 }
 
 size_t spec_words(int P, int D)

@@ -1,5 +1,5 @@
 // nd_fused_f32.cu -- instantiations of the fused on-chip kernel in FP32.
-#include "nd_field_impl.cuh"
+#include "nd_cluster.cuh"
 
 namespace nd {
 
@@ -50,6 +50,28 @@ cudaError_t launch_fused_f32(int P, const LaunchArgs &a)
     case 32: return launch_fused_p<32, float>(a);
     case 64: return launch_fused_p<64, float>(a);
     case 128: return launch_fused_p<128, float>(a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf)
+{
+    switch (P) {
+    case 16: return cluster_smem_bytes<16, float, kClusterCTAs>(D, Dpad, wbuf);
+    case 32: return cluster_smem_bytes<32, float, kClusterCTAs>(D, Dpad, wbuf);
+    case 64: return cluster_smem_bytes<64, float, kClusterCTAs>(D, Dpad, wbuf);
+    case 128: return cluster_smem_bytes<128, float, kClusterCTAs>(D, Dpad, wbuf);
+    default: return (size_t)-1;
+    }
+}
+
+cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad)
+{
+    switch (P) {
+    case 16: return launch_cluster_p<16, float>(a, maxD, maxDpad);
+    case 32: return launch_cluster_p<32, float>(a, maxD, maxDpad);
+    case 64: return launch_cluster_p<64, float>(a, maxD, maxDpad);
+    case 128: return launch_cluster_p<128, float>(a, maxD, maxDpad);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,5 +1,5 @@
 // nd_fused_f64.cu -- instantiations of the fused on-chip kernel in FP64.
-#include "nd_field_impl.cuh"
+#include "nd_cluster.cuh"
 
 namespace nd {
 
@@ -50,6 +50,28 @@ cudaError_t launch_fused_f64(int P, const LaunchArgs &a)
     case 32: return launch_fused_p<32, double>(a);
     case 64: return launch_fused_p<64, double>(a);
     case 128: return launch_fused_p<128, double>(a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t cluster_smem_f64(int P, int D, int Dpad, bool wbuf)
+{
+    switch (P) {
+    case 16: return cluster_smem_bytes<16, double, kClusterCTAs>(D, Dpad, wbuf);
+    case 32: return cluster_smem_bytes<32, double, kClusterCTAs>(D, Dpad, wbuf);
+    case 64: return cluster_smem_bytes<64, double, kClusterCTAs>(D, Dpad, wbuf);
+    case 128: return cluster_smem_bytes<128, double, kClusterCTAs>(D, Dpad, wbuf);
+    default: return (size_t)-1;
+    }
+}
+
+cudaError_t launch_cluster_f64(int P, const LaunchArgs &a, int maxD, int maxDpad)
+{
+    switch (P) {
+    case 16: return launch_cluster_p<16, double>(a, maxD, maxDpad);
+    case 32: return launch_cluster_p<32, double>(a, maxD, maxDpad);
+    case 64: return launch_cluster_p<64, double>(a, maxD, maxDpad);
+    case 128: return launch_cluster_p<128, double>(a, maxD, maxDpad);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -205,12 +205,16 @@ __device__ __forceinline__ void col_store(const cplx<T> *v, cplx<T> *col, int D,
 // two spectra with the mirror element, scale each by its diagonal kernel entry
 // and re-pack, ready for the inverse transform.
 template <int P, typename T>
+__device__ __forceinline__ void packed_col_fwd_loaded(cplx<T> *v, int c, const T *Ghat, int t, cplx<T> *scr,
+                                                      const cplx<T> *tw, unsigned gmask);
+
+template <int P, typename T>
 __device__ __forceinline__ void packed_col_fwd(cplx<T> *v, int c, bool active, int D, const cplx<T> *col,
                                                const T *Ghat, int t, int lane, cplx<T> *scr, const cplx<T> *tw,
                                                unsigned gmask)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
 #pragma unroll
     for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
 #pragma unroll
@@ -218,6 +222,16 @@ __device__ __forceinline__ void packed_col_fwd(cplx<T> *v, int c, bool active, i
         const int y = t + G * o;
         if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
     }
+    packed_col_fwd_loaded<P, T>(v, c, Ghat, t, scr, tw, gmask);
+}
+
+// The packed pair after loading (v = c0 + i c_{P/2}, rows < D, zero above).
+template <int P, typename T>
+__device__ __forceinline__ void packed_col_fwd_loaded(cplx<T> *v, int c, const T *Ghat, int t, cplx<T> *scr,
+                                                      const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH;
     fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
     mirror_put<P>(v, scr, t);
     __syncwarp(gmask);

@@ -1,0 +1,113 @@
+"""Single-disk stepping on a thread-block cluster (plan 200): each replica is
+spread over 8 CTAs whose shared memories hold its rows and exchange columns
+through distributed shared memory.  The per-element arithmetic is that of the
+one-CTA kernel, so trajectories match it, and they match the oracle's RK4 and
+stochastic Heun steps (Sec. II.C) to the field tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1207_2192_gb300 as nd
+from paper_1207_2192_gb300 import Disk, Nanodisk
+
+pytestmark = pytest.mark.gpu
+
+PLAN_CLUSTER = 200
+DISKS = [Disk(6e-9, 3e-9, alpha=0.02), Disk(13e-9, 3e-9, alpha=0.02), Disk(24e-9, 5e-9, alpha=0.02),
+         Disk(50e-9, 10e-9, alpha=0.02)]                    # P = 16, 32, 64, 128
+
+
+def cluster_handle(disks, reps, method):
+    h = Nanodisk(disks, reps, nd.ND_FP32)
+    ci = 0
+    while nd.nd_plan_info(h.h, ci) is not None:
+        nd.nd_set_plan(h.h, ci, method, PLAN_CLUSTER)
+        ci += 1
+    return h
+
+
+def run(h, method, n, X0=None):
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((h.B, 2)) if X0 is None else X0)
+    if method == nd.ND_METHOD_HEUN:
+        h.heun(m, n, 1e-14, np.full(h.B, 300.0), np.arange(h.B, dtype=np.uint64) + 11)
+    else:
+        h.rk4(m, n, 1e-14)
+    torch.cuda.synchronize()
+    return m
+
+
+@pytest.mark.parametrize("method", [nd.ND_METHOD_HEUN, nd.ND_METHOD_RK4])
+def test_cluster_plan_matches_one_cta_kernel(method):
+    reps = [3, 1, 2, 1]
+    X0 = np.array([[1e-9 * (i % 3), -0.5e-9 * (i % 2)] for i in range(sum(reps))])
+    ref = run(Nanodisk(DISKS, reps, nd.ND_FP32), method, 4, X0)
+    h = cluster_handle(DISKS, reps, method)
+    info = [nd.nd_plan_info(h.h, ci) for ci in range(4)]
+    key = "plan_heun" if method == nd.ND_METHOD_HEUN else "plan_rk4"
+    assert all(i[key] == PLAN_CLUSTER for i in info)
+    assert all(i["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] == 2048 for i in info)
+    out = run(h, method, 4, X0)
+    diff = (out - ref).abs().max().item()
+    assert diff <= 1e-6, diff
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+
+
+@pytest.mark.parametrize("R,L", [(13e-9, 3e-9), (24e-9, 5e-9), (50e-9, 10e-9)])
+def test_cluster_plan_matches_oracle(O, R, L):
+    disk = Disk(R, L, alpha=0.02, hext=(2e3, -1e3, 5e2))
+    model = O.Model(R, L, alpha=disk.alpha, hext=disk.hext)
+    g = model.init_vortex(2e-9 if R > 20e-9 else 0.5e-9, -1e-9 if R > 20e-9 else 0.0)
+    dt = 1e-14
+    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4)
+    start = h.unpack(h.to_device([g]))[0]
+    m = h.to_device([g])
+    h.rk4(m, 3, dt)
+    ref = model.rk4(start, 3, model.dtau(dt))
+    out = h.unpack(m)[0]
+    change = np.linalg.norm((ref - start) * model.mask)
+    floor = 1e-7 * np.sqrt(3 * model.C)
+    assert np.linalg.norm((out - ref) * model.mask) <= 2e-4 * change + floor
+    h = cluster_handle([disk], [2], nd.ND_METHOD_HEUN)
+    m = h.to_device([g, g])
+    h.heun(m, 3, dt, [300.0, 300.0], [21, 22], step0=5)
+    Ts = O.scaled_temperature(300.0, disk.A, disk.L)
+    for r, out in enumerate(h.unpack(m)):
+        ref = model.heun(start, 3, model.dtau(dt), Ts, 21 + r, 5)
+        change = np.linalg.norm((ref - start) * model.mask)
+        assert np.linalg.norm((out - ref) * model.mask) <= 2e-4 * change + floor
+
+
+def test_cluster_plan_with_mask_and_field_schedule(O):
+    """An elliptical mask and a per-step field schedule on the cluster plan,
+    against the oracle with the same mask and schedule."""
+    disk = Disk(40e-9, 8e-9, alpha=0.05)
+    model = O.Model(disk.R, disk.L, alpha=disk.alpha)
+    D = model.D
+    yy, xx = np.mgrid[0:D, 0:D]
+    c = 0.5 * (D - 1)
+    mask = (((xx - c) / (0.5 * D)) ** 2 + ((yy - c) / (0.35 * D)) ** 2 <= 1.0).astype(np.uint8)
+    sched = np.array([[1e4 * np.sin(0.3 * k), 5e3, -2e3] for k in range(6)])
+    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4)
+    h.set_mask(0, mask)
+    h.set_field_schedule(0, sched)
+    model.set_mask(mask)
+    model.set_schedule(sched)
+    g = model.init_vortex(1e-9, 1e-9)
+    start = h.unpack(h.to_device([g]))[0]
+    m = h.to_device([g])
+    h.rk4(m, 4, 1e-14)
+    ref = model.rk4(start, 4, model.dtau(1e-14))
+    out = h.unpack(m)[0]
+    mk = model.mask
+    change = np.linalg.norm((ref - start) * mk)
+    assert np.linalg.norm((out - ref) * mk) <= 2e-4 * change + 1e-7 * np.sqrt(3 * model.C)
+
+
+def test_cluster_plan_is_offered_by_autotune():
+    h = Nanodisk([Disk(50e-9, 10e-9, alpha=0.02)], [1], nd.ND_FP32)
+    assert nd.nd_set_plan(h.h, 0, nd.ND_METHOD_HEUN, PLAN_CLUSTER, check=False) == nd.ND_OK
+    big = Nanodisk([Disk(200e-9, 10e-9)], [1], nd.ND_FP32)            # P = 512: no cluster plan
+    assert nd.nd_set_plan(big.h, 0, nd.ND_METHOD_HEUN, PLAN_CLUSTER, check=False) == nd.ND_ERR_ARG
+    nd.nd_autotune(h.h, nd.ND_METHOD_HEUN, 1e-14, 5)
+    assert nd.nd_plan_info(h.h, 0)["plan_heun"] in (0, 1, 2, 100, PLAN_CLUSTER)
