@@ -3,28 +3,29 @@
 // replicas to fill the GPU with one CTA each.
 //
 // The replica's rows are split over the cluster: CTA k owns rows
-// [k rpc, (k+1) rpc) of the disk (rpc even, so z row pairs stay whole), and
-// holds those rows of the stage state, of the half spectrum and, afterwards,
-// of the field in its own shared memory.  Per field evaluation (Section II.B
-// convolution):
-//   1. forward rows: each CTA transforms its own rows (no communication);
+// [k rpc, (k+1) rpc) of the disk (rpc even, so z row pairs stay whole) and
+// the column slots [k spc, (k+1) spc) of the P/2 slots of the half spectrum
+// (slot 0: the real columns kx = 0 and P/2 packed as one complex column).
+// Per field evaluation (Section II.B convolution):
+//   1. forward rows: each CTA transforms its own rows and stores every
+//      spectrum entry straight into the shared memory of the CTA that owns
+//      its column (distributed shared memory stores: no thread waits on a
+//      remote load);
 //   2. cluster barrier;
-//   3. columns: CTA k takes column slots [k spc, (k+1) spc) of the P/2 slots
-//      (slot 0: the packed real columns kx = 0 and P/2), one FFT group per
-//      (slot, component); a group gathers its column from the owners' shared
-//      memory through distributed shared memory (DSMEM), transforms it,
-//      applies the spectral kernel (the x and y groups of a column exchange
-//      their spectra through local shared memory for the in-plane 2x2 block),
-//      transforms back and scatters the rows to their owners;
+//   3. columns: one FFT group per (slot, component) transforms its column
+//      from local shared memory, applies the spectral kernel (the x and y
+//      groups of a column exchange their spectra for the in-plane 2x2 block;
+//      the kernel's entries of the CTA's columns are staged in shared memory
+//      once per launch), transforms back and stores the rows into the shared
+//      memory of their owners;
 //   4. cluster barrier;
 //   5. inverse rows and the per-cell epilogue (stage_update) on the CTA's own
 //      rows; the next stage's forward rows read only those rows, so a CTA
-//      barrier suffices until the next column pass.
+//      barrier suffices until the next exchange.
 // The state y_n, the stage accumulator and the Heun predictor's normals of the
 // CTA's rows stay in its shared memory for the whole launch: global memory is
-// read once at the start and written once at the end.
-// The cluster barriers are hardware barriers of co-scheduled CTAs; nothing
-// spins on a flag.
+// read once at the start and written once at the end.  The cluster barriers
+// are hardware barriers of co-scheduled CTAs; nothing spins on a flag.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -41,6 +42,11 @@ template <int P, typename T, int NC> struct ClusterGeom {
     static constexpr int SPC = (P / 2) / NC;   // column slots per CTA
     static_assert(SPC >= 1 && (P / 2) % NC == 0, "column slots split evenly over the cluster");
     static_assert(3 * SPC <= NGRP, "one FFT group per (slot, component)");
+    static constexpr int KH = SpecGeom<P>::KH;
+    // column buffer stride (rows y < D <= P/2): the groups of a half warp read
+    // columns that start on different banks
+    static constexpr int CY = P / 2 + (G == 4 ? 4 : 8);
+    static constexpr int NTAB = SPC + 1;       // table slots: the CTA's columns, then kx = P/2
 };
 
 // Rows per CTA for a grid of D rows: even, so that z row pairs stay in one CTA.
@@ -52,22 +58,52 @@ __host__ __device__ __forceinline__ size_t cluster_smem_bytes(int D, int Dpad, b
     using CG = ClusterGeom<P, T, NC>;
     const int rpc = cluster_rows(D, NC);
     size_t b = sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G               // twiddles
+                                  + (size_t)3 * CG::SPC * CG::CY                        // column buffer
                                   + (size_t)3 * rpc * SpecGeom<P>::RS                   // spectrum rows
                                   + (size_t)CG::NGRP * FFTGeom<P>::SCRATCH);            // FFT scratch
+    b += sizeof(T) * (size_t)4 * CG::NTAB * CG::KH;                                     // kernel table
     b += sizeof(T) * (size_t)3 * rpc * Dpad * (wbuf ? 4 : 3);   // stage state, y_n, accumulator (+ normals)
+    b += 2 * sizeof(int);                                                               // own cell range
     return b;
+}
+
+// The packed real columns kx = 0 and P/2 of one component (v = c0 + i c_{P/2},
+// rows < D, zero above): forward transform, separation with the mirror
+// element, the diagonal kernel entries s0 (kx = 0) and s1 (kx = P/2) from
+// shared memory, and re-packing for the inverse transform.
+template <int P, typename T>
+__device__ __forceinline__ void cluster_packed_fwd(cplx<T> *v, const T *s0t, const T *s1t, int t, cplx<T> *scr,
+                                                   const cplx<T> *tw, unsigned gmask)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1;
+    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
+    mirror_put<P>(v, scr, t);
+    __syncwarp(gmask);
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int ky = t + G * o;
+        const int kyr = ky <= P / 2 ? ky : P - ky;
+        const cplx<T> w = mirror_get<P>(scr, ky);
+        const T h = T(0.5);
+        cplx<T> F0 = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
+        cplx<T> F1 = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
+        F0 = cscale(F0, s0t[kyr]);
+        F1 = cscale(F1, s1t[kyr]);
+        v[o] = {F0.x - F1.y, F0.y + F1.x};
+    }
+    __syncwarp(gmask);
 }
 
 template <int P, typename T, int MODE, int NC>
 __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
     k_cluster(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
-              const cplx<T> *__restrict__ twP, long long nsteps,
-              unsigned long long step_base, int use_wbuf)
+              const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base, int use_wbuf)
 {
     using Gm = FFTGeom<P>;
     using CG = ClusterGeom<P, T, NC>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH, NT = CG::NT, NGRP = CG::NGRP;
-    constexpr int SPC = CG::SPC;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = CG::KH, NT = CG::NT, NGRP = CG::NGRP;
+    constexpr int SPC = CG::SPC, CY = CG::CY, NTAB = CG::NTAB;
     static_assert(MODE == M_RK4 || MODE == M_HEUN, "stepping modes");
     cgc::cluster_group cluster = cgc::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -82,11 +118,14 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
     const long long lms = (long long)rpc * Dpad;                          // local state component stride
     const long long ms_s = (long long)D * Dpad;                           // global state component stride
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
-    cplx<T> *spec = tw + R1 * G;                                          // [3][rpc][RS]
+    cplx<T> *colbuf = tw + R1 * G;                                        // [3][SPC][CY]
+    cplx<T> *spec = colbuf + 3 * SPC * CY;                                // [3][rpc][RS]
     cplx<T> *scratch = spec + 3 * lcs;
-    T *msl = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);         // [3][rpc][Dpad]
+    T *gtab = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);        // [4][NTAB][KH]
+    T *msl = gtab + 4 * NTAB * KH;                                        // [3][rpc][Dpad]
     T *ynl = msl + 3 * lms, *accl = ynl + 3 * lms;
     T *wl = use_wbuf ? accl + 3 * lms : nullptr;
+    int *crange = reinterpret_cast<int *>((use_wbuf ? wl : accl) + 3 * lms);
     cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
     load_twiddles<P>(tw, twP, tid, NT);
     const V3Ptr<T> ms{msl, lms}, wb{wl, lms}, ynv{ynl, lms}, accv{accl, lms}, none{nullptr, 0};
@@ -99,23 +138,43 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
         ms.st(mi, m0);
         ynv.st(mi, m0);
     }
+    // the kernel's entries of the CTA's columns (and of kx = P/2), from the
+    // component-major copy of the table
+    {
+        constexpr int KK = KH * KH;
+        const T *Gc = reinterpret_cast<const T *>(r.Ghat) + 4 * KK;
+        for (int i = tid; i < 4 * NTAB * KH; i += NT) {
+            const int c = i / (NTAB * KH), rem = i - c * (NTAB * KH), j = rem / KH, ky = rem - j * KH;
+            const int kx = j < SPC ? rank * SPC + j : P / 2;
+            gtab[i] = __ldg(Gc + (long long)c * KK + kx * KH + ky);
+        }
+    }
+    // the CTA's cells: a contiguous range of the ascending cell list
+    if (tid == 0) {
+        int lo = 0, hi = r.ncells;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(r.cells + mid) < ylo * D) lo = mid + 1; else hi = mid; }
+        crange[0] = lo;
+        hi = r.ncells;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(r.cells + mid) < (ylo + nloc) * D) lo = mid + 1; else hi = mid; }
+        crange[1] = lo;
+    }
     // row tasks of this CTA: xy rows 0..nloc-1, then z pairs (0,1), (2,3), ...
     const int nrt = nloc + (nloc + 1) / 2;
+    const int nrounds = (nrt + NGRP - 1) / NGRP;
     // column task of this group: slot j (column kx = rank SPC + j, slot 0 of
     // rank 0 being the packed pair), component c
     const int cj = gid.group % SPC, cc = gid.group / SPC;
     const bool ctask = gid.group < 3 * SPC;   // groups beyond 3 SPC idle in the column pass
     const int kslot = rank * SPC + cj;
     const bool packed = ctask && kslot == 0;
-    const T *Ghat = reinterpret_cast<const T *>(r.Ghat);
-    __syncthreads();
+    cluster.sync();   // every CTA of the cluster runs (its shared memory exists) before the first remote store
+    const int c0 = crange[0], c1 = crange[1];
 
     for (long long n = 0; n < nsteps; ++n) {
         const unsigned long long step = step_base + r.step0 + (unsigned long long)n;
         for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
-            // 1. forward rows of the CTA's own rows
-            for (int qb = gid.group; qb < ((nrt + NGRP - 1) / NGRP) * NGRP; qb += NGRP) {
-                const int q = qb;
+            // 1. forward rows of the CTA's own rows, sent to the column owners
+            for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
                 const bool isxy = q < nloc;
                 const int l0 = isxy ? q : 2 * (q - nloc), l1 = l0 + 1;
@@ -132,28 +191,60 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                                      hasB ? msl[2 * lms + (long long)l1 * Dpad + x] : T(0)};
                     }
                 }
-                cplx<T> *dA = isxy ? spec + (long long)l0 * RS : spec + 2 * lcs + (long long)l0 * RS;
-                cplx<T> *dB = isxy ? spec + lcs + (long long)l0 * RS : spec + 2 * lcs + (long long)l1 * RS;
-                row_fwd_core<P, T>(v, act, dA, dB, hasB, gid.t, scr, tw, gid.gmask);
+                fft_group<P, -1, FFT_HALF_IN>(v, gid.t, scr, tw, gid.gmask);
+                mirror_put<P>(v, scr, gid.t);
+                __syncwarp(gid.gmask);
+                if (act) {
+                    // A: the row ending in the real part (x, or the first z row),
+                    // B: the one ending in the imaginary part (y, or the second z row)
+                    const int cA = isxy ? 0 : 2, cB = isxy ? 1 : 2;
+                    const int yA = ylo + l0, yB = isxy ? ylo + l0 : ylo + l1;
+                    T rA0 = T(0), rB0 = T(0);   // lane t = 0: the real entries at k = 0 (then k = P/2)
+#pragma unroll
+                    for (int o = 0; o < R1; ++o) {
+                        const int k = gid.t + G * o;
+                        if (k <= P / 2) {
+                            const cplx<T> w = mirror_get<P>(scr, k);
+                            const T h = T(0.5);
+                            const cplx<T> A = {h * (v[o].x + w.x), h * (v[o].y - w.y)};
+                            const cplx<T> B = {h * (v[o].y + w.y), -h * (v[o].x - w.x)};
+                            if (k == 0) {
+                                rA0 = A.x;
+                                rB0 = B.x;
+                            } else if (k == P / 2) {
+                                cplx<T> *dst = cluster.map_shared_rank(colbuf, 0);
+                                dst[(cA * SPC) * CY + yA] = {rA0, A.x};
+                                if (hasB) dst[(cB * SPC) * CY + yB] = {rB0, B.x};
+                            } else {
+                                const int ow = k / SPC, j = k - ow * SPC;
+                                cplx<T> *dst = cluster.map_shared_rank(colbuf, ow);
+                                dst[(cA * SPC + j) * CY + yA] = A;
+                                if (hasB) dst[(cB * SPC + j) * CY + yB] = B;
+                            }
+                        }
+                    }
+                }
+                __syncwarp(gid.gmask);
             }
-            cluster.sync();   // every row of every CTA transformed
-            // 3. columns, gathered from and scattered to the owners
+            cluster.sync();   // every row spectrum with its column owner
+            // 3. columns from the local column buffer, back to the row owners
             {
                 cplx<T> v[R1];
 #pragma unroll
                 for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
                 const int kx = packed ? 0 : kslot;
+                if (ctask) {
+                    const cplx<T> *col = colbuf + (cc * SPC + cj) * CY;
 #pragma unroll
-                for (int o = 0; o < R1 / 2; ++o) {
-                    const int y = gid.t + G * o;
-                    if (ctask && y < D) {
-                        const int ow = y / rpc, lr = y - ow * rpc;   // the row's owner
-                        const cplx<T> *src = cluster.map_shared_rank(spec + cc * lcs + (long long)lr * RS, ow);
-                        v[o] = packed ? cplx<T>{src[0].x, src[P / 2].x} : src[kx];
+                    for (int o = 0; o < R1 / 2; ++o) {
+                        const int y = gid.t + G * o;
+                        if (y < D) v[o] = col[y];
                     }
                 }
                 if (packed) {
-                    packed_col_fwd_loaded<P, T>(v, cc, Ghat, gid.t, scr, tw, gid.gmask);
+                    const int comp = cc == 2 ? 3 : cc;   // the diagonal entry: xx, yy or zz
+                    cluster_packed_fwd<P, T>(v, gtab + (comp * NTAB) * KH, gtab + (comp * NTAB + SPC) * KH, gid.t,
+                                             scr, tw, gid.gmask);
                 } else if (ctask) {
                     fft_group<P, -1, FFT_HALF_IN>(v, gid.t, scr, tw, gid.gmask);
                 }
@@ -164,28 +255,26 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                 }
                 __syncthreads();
                 if (ctask && !packed) {
-                    constexpr int KK = KH * KH;
-                    const T *Gs = Ghat + 4 * KK + kx * KH;   // component-major copy of the table
                     if (cc < 2) {
                         const cplx<T> *other = scratch + ((1 - cc) * SPC + cj) * Gm::SCRATCH;
-                        const T *gd = Gs + cc * KK, *go = Gs + 2 * KK;
+                        const T *gd = gtab + (cc * NTAB + cj) * KH, *go = gtab + (2 * NTAB + cj) * KH;
 #pragma unroll
                         for (int o = 0; o < R1; ++o) {
                             const int ky = gid.t + G * o;
                             const bool up = ky <= P / 2;
                             const int kyr = up ? ky : P - ky;
-                            const T gdiag = __ldg(gd + kyr), gxy0 = __ldg(go + kyr);
+                            const T gdiag = gd[kyr], gxy0 = go[kyr];
                             const T gxy = up ? gxy0 : -gxy0;   // G_xy is odd in ky
                             const cplx<T> w = other[o * G + gid.t];
                             v[o] = cc == 0 ? tensor_row(gdiag, v[o], gxy, w) : tensor_row(gxy, w, gdiag, v[o]);
                         }
                     } else {
-                        const T *gz = Gs + 3 * KK;
+                        const T *gz = gtab + (3 * NTAB + cj) * KH;
 #pragma unroll
                         for (int o = 0; o < R1; ++o) {
                             const int ky = gid.t + G * o;
                             const int kyr = ky <= P / 2 ? ky : P - ky;
-                            v[o] = cscale(v[o], __ldg(gz + kyr));
+                            v[o] = cscale(v[o], gz[kyr]);
                         }
                     }
                 }
@@ -195,7 +284,7 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                 for (int o = 0; o < R1 / 2; ++o) {
                     const int y = gid.t + G * o;
                     if (ctask && y < D) {
-                        const int ow = y / rpc, lr = y - ow * rpc;
+                        const int ow = y / rpc, lr = y - ow * rpc;   // the row's owner
                         cplx<T> *dst = cluster.map_shared_rank(spec + cc * lcs + (long long)lr * RS, ow);
                         if (packed) {
                             dst[0] = {v[o].x, T(0)};
@@ -208,8 +297,7 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
             }
             cluster.sync();   // every column back with its owner
             // 5. inverse rows of the CTA's own rows (the field rows, in place)
-            for (int qb = gid.group; qb < ((nrt + NGRP - 1) / NGRP) * NGRP; qb += NGRP) {
-                const int q = qb;
+            for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
                 const bool isxy = q < nloc;
                 const int l0 = isxy ? q : 2 * (q - nloc), l1 = l0 + 1;
@@ -231,13 +319,13 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                 }
             }
             __syncthreads();
-            // the per-cell epilogue of the CTA's own cells
+            // the per-cell epilogue of the CTA's cells
             const StepParams<T> sp = step_params<T>(r);
             const vec3<T> cx = step_chext<T>(r, sp, step);
             const T *hr = reinterpret_cast<const T *>(spec);
-            for (int i = tid; i < nloc * D; i += NT) {
-                const int lr = i / D, x = i - lr * D, y = ylo + lr, cell = y * D + x;
-                if (!r.mask[cell]) continue;
+            for (int k = c0 + tid; k < c1; k += NT) {
+                const int cell = __ldg(r.cells + k);
+                const int y = cell / D, x = cell - y * D, lr = y - ylo;
                 const long long mi = (long long)lr * Dpad + x;
                 const long long hi = (long long)lr * (2 * RS) + x;
                 const vec3<T> b = {hr[hi] + cx.x, hr[2 * lcs + hi] + cx.y, hr[4 * lcs + hi] + cx.z};
@@ -247,11 +335,12 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
         }
     }
     // the final state of the CTA's cells back to the caller's buffer
-    for (int i = tid; i < nloc * D; i += NT) {
-        const int lr = i / D, x = i - lr * D, y = ylo + lr;
-        if (r.mask[y * D + x]) yg.st((long long)y * Dpad + x, ynv.ld((long long)lr * Dpad + x));
+    for (int k = c0 + tid; k < c1; k += NT) {
+        const int cell = __ldg(r.cells + k);
+        const int y = cell / D, x = cell - y * D;
+        yg.st((long long)y * Dpad + x, ynv.ld((long long)(y - ylo) * Dpad + x));
     }
-    cluster.sync();   // no CTA leaves while another may still read its shared memory
+    cluster.sync();   // no CTA leaves while another may still access its shared memory
 }
 
 // The cluster size of the on-chip sizes.
