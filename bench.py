@@ -71,7 +71,8 @@ def device_sms(device=0):
 # unit and the device headers it includes (nd_kernels.h holds only host
 # declarations and is left out).
 KERNEL_SOURCES = {
-    "batched_heun": ["nd_fused_f32.cu", "nd_field_impl.cuh", "nd_phases.cuh", "nd_fft.cuh", "nd_common.cuh"],
+    "batched_heun": ["nd_fused_f32.cu", "nd_cluster.cuh", "nd_field_impl.cuh", "nd_phases.cuh", "nd_fft.cuh",
+                     "nd_common.cuh"],
     "large_disk": ["nd_glob_f32.cu", "nd_field_impl.cuh", "nd_phases.cuh", "nd_fft.cuh", "nd_common.cuh"],
 }
 KERNEL_SOURCES["plain"] = KERNEL_SOURCES["batched_heun"]
@@ -177,6 +178,9 @@ class Workload:
         self.disk = nd.Disk(w["R"], w["L"], alpha=ALPHA)
         self.B = w["B"]
         self.h = nd.Nanodisk([self.disk], [self.B], nd.ND_FP32)
+        # the stepping plan of the size class: the public autotuner times the
+        # one-CTA kernel's thread counts, the cluster plan and the global path
+        nd.nd_autotune(self.h.h, nd.ND_METHOD_HEUN, DT, 10)
         L0 = self.h.layout[0]
         self.D, self.P, self.C = L0["D"], L0["P"], L0["cells"]
         self.m = self.h.empty_device()
@@ -246,6 +250,8 @@ def kernel_name(wl):
     the handle uses (fused on-chip kernel with its thread count, or the global
     path)."""
     info = wl.nd.nd_plan_info(wl.h.h, 0)
+    if info and info["plan_heun"] == 200:
+        return f"k_cluster<{wl.P},float,HEUN,8> (one replica per 8-CTA cluster)"
     if info and info["threads_heun"] > 0:
         return f"k_fused<{wl.P},float,HEUN,{info['threads_heun']}>"
     return "global-path Heun step (k_g_rows, k_g_cols_tile x/y and z, k_g_epi)"
@@ -404,7 +410,7 @@ def plain_number(args):
         wl.run_step()
     b.record()
     torch.cuda.synchronize()
-    return wl.cell_updates_per_step() * n / (a.elapsed_time(b) / 1e3)
+    return wl.cell_updates_per_step() * n / (a.elapsed_time(b) / 1e3), kernel_name(wl)
 
 
 # ---------------------------------------------------------------- oracle
@@ -489,8 +495,8 @@ def main():
     result, wl = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_plain and args.workload == "batched_heun":
-            plain = plain_number(args)
-            result["plain"] = {"value": plain, "unit": "cell-updates/s", "replicas": 1,
+            plain, plain_kernel = plain_number(args)
+            result["plain"] = {"value": plain, "unit": "cell-updates/s", "replicas": 1, "kernel": plain_kernel,
                                "batched_over_plain": result["value"] / world / plain}
         if not args.no_cpu_baseline:
             rate, sample, cores = oracle_rate(args.workload)

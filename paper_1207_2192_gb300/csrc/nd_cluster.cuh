@@ -67,17 +67,16 @@ __host__ __device__ __forceinline__ size_t cluster_smem_bytes(int D, int Dpad, b
     return b;
 }
 
-// The packed real columns kx = 0 and P/2 of one component (v = c0 + i c_{P/2},
-// rows < D, zero above): forward transform, separation with the mirror
-// element, the diagonal kernel entries s0 (kx = 0) and s1 (kx = P/2) from
-// shared memory, and re-packing for the inverse transform.
+// The spectral step of the packed real columns kx = 0 and P/2 of one
+// component after the forward transform of c0 + i c_{P/2}: separation with
+// the mirror element, the diagonal kernel entries s0 (kx = 0) and s1
+// (kx = P/2) from shared memory, and re-packing for the inverse transform.
 template <int P, typename T>
-__device__ __forceinline__ void cluster_packed_fwd(cplx<T> *v, const T *s0t, const T *s1t, int t, cplx<T> *scr,
-                                                   const cplx<T> *tw, unsigned gmask)
+__device__ __forceinline__ void cluster_packed_scale(cplx<T> *v, const T *s0t, const T *s1t, int t, cplx<T> *scr,
+                                                     unsigned gmask)
 {
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1;
-    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
     mirror_put<P>(v, scr, t);
     __syncwarp(gmask);
 #pragma unroll
@@ -241,12 +240,13 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                         if (y < D) v[o] = col[y];
                     }
                 }
+                // one transform call for both kinds of column, so that a warp
+                // holding the packed slot does not run two transforms in turn
+                if (ctask) fft_group<P, -1, FFT_HALF_IN>(v, gid.t, scr, tw, gid.gmask);
                 if (packed) {
                     const int comp = cc == 2 ? 3 : cc;   // the diagonal entry: xx, yy or zz
-                    cluster_packed_fwd<P, T>(v, gtab + (comp * NTAB) * KH, gtab + (comp * NTAB + SPC) * KH, gid.t,
-                                             scr, tw, gid.gmask);
-                } else if (ctask) {
-                    fft_group<P, -1, FFT_HALF_IN>(v, gid.t, scr, tw, gid.gmask);
+                    cluster_packed_scale<P, T>(v, gtab + (comp * NTAB) * KH, gtab + (comp * NTAB + SPC) * KH, gid.t,
+                                               scr, gid.gmask);
                 }
                 // the x and y groups of a column exchange their spectra
                 if (ctask && !packed && cc < 2) {

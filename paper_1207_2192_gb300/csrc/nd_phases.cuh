@@ -225,14 +225,16 @@ __device__ __forceinline__ void packed_col_fwd(cplx<T> *v, int c, bool active, i
     packed_col_fwd_loaded<P, T>(v, c, Ghat, t, scr, tw, gmask);
 }
 
-// The packed pair after loading (v = c0 + i c_{P/2}, rows < D, zero above).
+// The spectral step of a packed pair after its forward transform (v holds
+// the transform of c0 + i c_{P/2}): separate the two column spectra with the
+// mirror element, scale each by its diagonal kernel entry (s0 at kx = 0, s1 at
+// kx = P/2) and re-pack them for the inverse transform.
 template <int P, typename T>
-__device__ __forceinline__ void packed_col_fwd_loaded(cplx<T> *v, int c, const T *Ghat, int t, cplx<T> *scr,
-                                                      const cplx<T> *tw, unsigned gmask)
+__device__ __forceinline__ void packed_col_scale(cplx<T> *v, int c, const T *Ghat, int t, cplx<T> *scr,
+                                                 unsigned gmask)
 {
     using Gm = FFTGeom<P>;
     constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH;
-    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
     mirror_put<P>(v, scr, t);
     __syncwarp(gmask);
 #pragma unroll
@@ -253,6 +255,15 @@ __device__ __forceinline__ void packed_col_fwd_loaded(cplx<T> *v, int c, const T
     __syncwarp(gmask);
 }
 
+// The packed pair after loading (v = c0 + i c_{P/2}, rows < D, zero above).
+template <int P, typename T>
+__device__ __forceinline__ void packed_col_fwd_loaded(cplx<T> *v, int c, const T *Ghat, int t, cplx<T> *scr,
+                                                      const cplx<T> *tw, unsigned gmask)
+{
+    fft_group<P, -1, FFT_HALF_IN>(v, t, scr, tw, gmask);
+    packed_col_scale<P, T>(v, c, Ghat, t, scr, gmask);
+}
+
 // Rows < D of the inverse-transformed packed pair back to the two real columns.
 template <int P, typename T>
 __device__ __forceinline__ void packed_col_store(const cplx<T> *v, bool active, int D, cplx<T> *col, int t)
@@ -270,43 +281,69 @@ __device__ __forceinline__ void packed_col_store(const cplx<T> *v, bool active, 
     }
 }
 
+// Loads and stores of a column task of either kind (pk: the packed pair).
+template <int P, typename T>
+__device__ __forceinline__ void col_load_kind(cplx<T> *v, const cplx<T> *col, bool pk, int kx, int D, int t,
+                                              bool active)
+{
+    using Gm = FFTGeom<P>;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS;
+    if (pk) {
+#pragma unroll
+        for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+        for (int o = 0; o < R1 / 2; ++o) {
+            const int y = t + G * o;
+            if (active && y < D) v[o] = {col[(long long)y * RS].x, col[(long long)y * RS + P / 2].x};
+        }
+    } else {
+        col_load<P>(v, col + kx, D, t, active);
+    }
+}
+template <int P, typename T>
+__device__ __forceinline__ void col_store_kind(const cplx<T> *v, cplx<T> *col, bool pk, int kx, int D, int t,
+                                               bool active)
+{
+    if (pk) packed_col_store<P, T>(v, active, D, col, t);
+    else col_store<P>(v, col + kx, D, t, active);
+}
+
 // Column task q = 0..P/2-1: q = 0 is the packed pair of real columns kx = 0
-// and kx = P/2, q >= 1 is column kx = q.
+// and kx = P/2, q >= 1 is column kx = q.  Both kinds run the same transform
+// calls (x and y, then z), and only the loads, the spectral step and the
+// stores differ, so that the groups of one warp never run the transforms of
+// the two kinds one after the other.
 template <int P, typename T>
 __device__ __forceinline__ void col_task(int q, bool active, int D, cplx<T> *spec, long long cstride,
                                          const T *Ghat, int t, int lane, cplx<T> *scr, const cplx<T> *tw,
                                          unsigned gmask)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = SpecGeom<P>::KH;
-    if (q > 0) {
-        const int kx = active ? q : 1;   // idle groups still run the transforms; keep their table reads in range
-        cplx<T> vx[R1], vy[R1];
-        col_load<P>(vx, spec + kx, D, t, active);
-        col_load<P>(vy, spec + cstride + kx, D, t, active);
-        fft_group<P, -1, FFT_HALF_IN>(vx, t, scr, tw, gmask);
-        fft_group<P, -1, FFT_HALF_IN>(vy, t, scr, tw, gmask);
+    constexpr int R1 = Gm::R1;
+    const bool pk = q == 0;
+    const int kx = pk ? 0 : (active ? q : 1);   // idle groups still run the transforms; keep their table reads in range
+    cplx<T> vx[R1], vy[R1];
+    col_load_kind<P, T>(vx, spec, pk, kx, D, t, active);
+    col_load_kind<P, T>(vy, spec + cstride, pk, kx, D, t, active);
+    fft_group<P, -1, FFT_HALF_IN>(vx, t, scr, tw, gmask);
+    fft_group<P, -1, FFT_HALF_IN>(vy, t, scr, tw, gmask);
+    if (pk) {   // G_xy vanishes on both real columns
+        packed_col_scale<P, T>(vx, 0, Ghat, t, scr, gmask);
+        packed_col_scale<P, T>(vy, 1, Ghat, t, scr, gmask);
+    } else {
         col_multiply<P>(vx, vy, Ghat, kx, t);
-        fft_group<P, +1, FFT_HALF_OUT>(vx, t, scr, tw, gmask);
-        fft_group<P, +1, FFT_HALF_OUT>(vy, t, scr, tw, gmask);
-        col_store<P>(vx, spec + kx, D, t, active);
-        col_store<P>(vy, spec + cstride + kx, D, t, active);
-        cplx<T> vz[R1];
-        col_load<P>(vz, spec + 2 * cstride + kx, D, t, active);
-        fft_group<P, -1, FFT_HALF_IN>(vz, t, scr, tw, gmask);
-        col_multiply_z<P>(vz, Ghat, kx, t);
-        fft_group<P, +1, FFT_HALF_OUT>(vz, t, scr, tw, gmask);
-        col_store<P>(vz, spec + 2 * cstride + kx, D, t, active);
-        return;
     }
-    // packed real columns: z = c0 + i c_{P/2}; G_xy vanishes on both columns
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        cplx<T> v[R1];
-        packed_col_fwd<P, T>(v, c, active, D, spec + c * cstride, Ghat, t, lane, scr, tw, gmask);
-        fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gmask);
-        packed_col_store<P, T>(v, active, D, spec + c * cstride, t);
-    }
+    fft_group<P, +1, FFT_HALF_OUT>(vx, t, scr, tw, gmask);
+    fft_group<P, +1, FFT_HALF_OUT>(vy, t, scr, tw, gmask);
+    col_store_kind<P, T>(vx, spec, pk, kx, D, t, active);
+    col_store_kind<P, T>(vy, spec + cstride, pk, kx, D, t, active);
+    cplx<T> vz[R1];
+    col_load_kind<P, T>(vz, spec + 2 * cstride, pk, kx, D, t, active);
+    fft_group<P, -1, FFT_HALF_IN>(vz, t, scr, tw, gmask);
+    if (pk) packed_col_scale<P, T>(vz, 2, Ghat, t, scr, gmask);
+    else col_multiply_z<P>(vz, Ghat, kx, t);
+    fft_group<P, +1, FFT_HALF_OUT>(vz, t, scr, tw, gmask);
+    col_store_kind<P, T>(vz, spec + 2 * cstride, pk, kx, D, t, active);
 }
 
 // ---------------------------------------------------------------- row inv

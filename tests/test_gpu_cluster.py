@@ -17,8 +17,8 @@ DISKS = [Disk(6e-9, 3e-9, alpha=0.02), Disk(13e-9, 3e-9, alpha=0.02), Disk(24e-9
          Disk(50e-9, 10e-9, alpha=0.02)]                    # P = 16, 32, 64, 128
 
 
-def cluster_handle(disks, reps, method):
-    h = Nanodisk(disks, reps, nd.ND_FP32)
+def cluster_handle(disks, reps, method, prec=nd.ND_FP32):
+    h = Nanodisk(disks, reps, prec)
     ci = 0
     while nd.nd_plan_info(h.h, ci) is not None:
         nd.nd_set_plan(h.h, ci, method, PLAN_CLUSTER)
@@ -53,29 +53,38 @@ def test_cluster_plan_matches_one_cta_kernel(method):
     assert nd.nd_check_status(h.h) == nd.ND_OK
 
 
+TOL = {nd.ND_FP32: 1e-5, nd.ND_FP64: 1e-11}      # relative field error of each precision
+
+
+def traj_ok(out, ref, start, model, prec):
+    """Trajectory error against 20x the field tolerance times the change over
+    the run, plus the rounding of the stored state."""
+    change = np.linalg.norm((ref - start) * model.mask)
+    floor = (1e-7 if prec == nd.ND_FP32 else 1e-15) * np.sqrt(3 * model.C)
+    return np.linalg.norm((out - ref) * model.mask) <= 20 * TOL[prec] * change + floor
+
+
+@pytest.mark.parametrize("prec", [nd.ND_FP32, nd.ND_FP64])
 @pytest.mark.parametrize("R,L", [(13e-9, 3e-9), (24e-9, 5e-9), (50e-9, 10e-9)])
-def test_cluster_plan_matches_oracle(O, R, L):
+def test_cluster_plan_matches_oracle(O, R, L, prec):
     disk = Disk(R, L, alpha=0.02, hext=(2e3, -1e3, 5e2))
     model = O.Model(R, L, alpha=disk.alpha, hext=disk.hext)
     g = model.init_vortex(2e-9 if R > 20e-9 else 0.5e-9, -1e-9 if R > 20e-9 else 0.0)
     dt = 1e-14
-    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4)
+    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4, prec)
+    assert nd.nd_plan_info(h.h, 0)["plan_rk4"] == PLAN_CLUSTER
     start = h.unpack(h.to_device([g]))[0]
     m = h.to_device([g])
     h.rk4(m, 3, dt)
     ref = model.rk4(start, 3, model.dtau(dt))
-    out = h.unpack(m)[0]
-    change = np.linalg.norm((ref - start) * model.mask)
-    floor = 1e-7 * np.sqrt(3 * model.C)
-    assert np.linalg.norm((out - ref) * model.mask) <= 2e-4 * change + floor
-    h = cluster_handle([disk], [2], nd.ND_METHOD_HEUN)
+    assert traj_ok(h.unpack(m)[0], ref, start, model, prec)
+    h = cluster_handle([disk], [2], nd.ND_METHOD_HEUN, prec)
     m = h.to_device([g, g])
     h.heun(m, 3, dt, [300.0, 300.0], [21, 22], step0=5)
     Ts = O.scaled_temperature(300.0, disk.A, disk.L)
     for r, out in enumerate(h.unpack(m)):
         ref = model.heun(start, 3, model.dtau(dt), Ts, 21 + r, 5)
-        change = np.linalg.norm((ref - start) * model.mask)
-        assert np.linalg.norm((out - ref) * model.mask) <= 2e-4 * change + floor
+        assert traj_ok(out, ref, start, model, prec)
 
 
 def test_cluster_plan_with_mask_and_field_schedule(O):
@@ -98,10 +107,7 @@ def test_cluster_plan_with_mask_and_field_schedule(O):
     m = h.to_device([g])
     h.rk4(m, 4, 1e-14)
     ref = model.rk4(start, 4, model.dtau(1e-14))
-    out = h.unpack(m)[0]
-    mk = model.mask
-    change = np.linalg.norm((ref - start) * mk)
-    assert np.linalg.norm((out - ref) * mk) <= 2e-4 * change + 1e-7 * np.sqrt(3 * model.C)
+    assert traj_ok(h.unpack(m)[0], ref, start, model, nd.ND_FP32)
 
 
 def test_cluster_plan_is_offered_by_autotune():
