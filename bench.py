@@ -250,8 +250,9 @@ def kernel_name(wl):
     the handle uses (fused on-chip kernel with its thread count, or the global
     path)."""
     info = wl.nd.nd_plan_info(wl.h.h, 0)
-    if info and info["plan_heun"] == 200:
-        return f"k_cluster<{wl.P},float,HEUN,8> (one replica per 8-CTA cluster)"
+    if info and info["plan_heun"] in (200, 201):
+        nc = info["threads_heun"] // 256
+        return f"k_cluster<{wl.P},float,HEUN,{nc}> (one replica per {nc}-CTA cluster)"
     if info and info["threads_heun"] > 0:
         return f"k_fused<{wl.P},float,HEUN,{info['threads_heun']}>"
     return "global-path Heun step (k_g_rows, k_g_cols_tile x/y and z, k_g_epi)"

@@ -323,21 +323,21 @@ int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_
  * on-chip kernel with one of up to three thread counts (which set how many
  * FFT groups share the row and column passes), on the global-memory path, or
  * (P <= 128) with each replica spread over a thread-block cluster of 8 CTAs
- * whose shared memories hold the replica's rows and exchange columns through
- * distributed shared memory (for classes with too few replicas to fill the
- * GPU with one CTA each).
+ * (or 16 for P >= 32) whose shared memories hold the replica's rows and
+ * exchange columns through distributed shared memory (for classes with too
+ * few replicas to fill the GPU with one CTA each).
  * nd_autotune times every candidate that fits, on a scratch copy of an
  * analytic vortex state, for n_steps steps of the given method (and, for
  * Heun, 300 K), and keeps the fastest per class for later nd_step_* calls and
  * graphs.  nd_plan_info reports, for class cls (0-based, in order of first
  * appearance), its P, replica count, the chosen plans (-1 default, 0..2 fused
- * variant, 100 global path, 200 cluster) and the threads per replica (fused:
+ * variant, 100 global path, 200/201 cluster of 8/16 CTAs) and the threads per replica (fused:
  * threads per CTA; cluster: threads of the cluster; 0: global path).  Returns
  * ND_ERR_ARG for cls out of range.  The paper has no counterpart. */
 int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream);
 /* Force the plan of class cls for a method (-1 default, 0..2 fused variant,
- * 100 global path, 200 cluster); ND_ERR_ARG if it does not exist or does not
- * fit.  Plans 0..2 and 100 compute the same arithmetic per element, so
+ * 100 global path, 200 cluster of 8 CTAs, 201 cluster of 16 CTAs); ND_ERR_ARG
+ * if it does not exist or does not fit.  Plans 0..2 and 100 compute the same arithmetic per element, so
  * trajectories do not depend on which of them runs; the cluster plan splits
  * the column products over the x and y groups and agrees with them to
  * rounding (a few units in the last place of FP32 per step). */

@@ -82,7 +82,9 @@ struct SizeClass {
 };
 
 constexpr int kPlanGlobal = 100;
-constexpr int kPlanCluster = 200;   // one replica per thread-block cluster of 8 CTAs (P <= 128)
+constexpr int kPlanCluster = 200;     // one replica per thread-block cluster of 8 CTAs (P <= 128)
+constexpr int kPlanCluster16 = 201;   // one replica per cluster of 16 CTAs (32 <= P <= 128)
+static int plan_cluster_nc(int pl) { return pl == kPlanCluster ? 8 : pl == kPlanCluster16 ? 16 : 0; }
 
 int next_pow2_at_least(int n)
 {
@@ -261,6 +263,15 @@ static void build_segments(int Bc, long long n, int ncta, std::vector<SegmentHos
     off[ncta] = (int)segs.size();
 }
 
+// Whether a cluster plan of nc CTAs per replica exists for the class: the
+// size has one, its shared memory fits, and the GPU can hold such a cluster.
+static bool cluster_plan_fits(const nd_handle *h, const SizeClass &c, int prec, bool heun, int nc)
+{
+    const size_t sm = cluster_smem(c.P, prec, c.maxD, c.maxDpad, heun, nc);
+    if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return false;
+    return cluster_max_active(c.P, prec, c.maxD, c.maxDpad, heun, nc) > 0;
+}
+
 // Run one mode over all replicas.  fp64 selects the FP64 kernels (with y a
 // double buffer of the state layout), otherwise the handle precision.
 static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long long nsteps, cudaStream_t st,
@@ -287,17 +298,17 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         bool fused = fp64 ? c.fused_fp64 : c.fused_main;
         const bool stepping = (mode == M_HEUN || mode == M_RK4) && !fp64;
         int variant = 0;
-        bool cluster = false;
+        int cluster_nc = 0;
         if (stepping) {
             const int pl = c.plan[mode == M_RK4 ? 0 : 1];
             if (pl == kPlanGlobal) fused = false;
-            else if (pl == kPlanCluster) cluster = true;
+            else if (plan_cluster_nc(pl)) cluster_nc = plan_cluster_nc(pl);
             else if (pl > 0) variant = pl;
         }
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
-        if (cluster) {
+        if (cluster_nc) {
             a.use_wbuf = mode == M_HEUN ? 1 : 0;
-            ND_CUDA(launch_cluster(c.P, prec, a, c.maxD, c.maxDpad));
+            ND_CUDA(launch_cluster(c.P, prec, a, c.maxD, c.maxDpad, cluster_nc));
         } else if (fused) {
             a.smem = fp64 ? c.smem_fp64 : c.smem_main;
             a.status = h->status_d;
@@ -1295,10 +1306,8 @@ int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, 
             if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(v);
         }
         cands.push_back(kPlanGlobal);
-        {
-            const size_t sm = cluster_smem(c.P, prec, c.maxD, c.maxDpad, mode == M_HEUN);
-            if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(kPlanCluster);
-        }
+        for (int pl : {kPlanCluster, kPlanCluster16})
+            if (cluster_plan_fits(h, c, prec, mode == M_HEUN, plan_cluster_nc(pl))) cands.push_back(pl);
         float best_ms = 1e30f;
         int best = cands.front();
         for (int cand : cands) {
@@ -1331,9 +1340,9 @@ int nd_set_plan(nd_handle *h, int cls, int method, int plan)
     if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
     SizeClass &c = h->classes[cls];
     const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
-    if (plan == kPlanCluster) {
-        const size_t sm = cluster_smem(c.P, prec, c.maxD, c.maxDpad, method == ND_METHOD_HEUN);
-        if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return fail(ND_ERR_ARG, "no cluster plan for this size class");
+    if (plan_cluster_nc(plan)) {
+        if (!cluster_plan_fits(h, c, prec, method == ND_METHOD_HEUN, plan_cluster_nc(plan)))
+            return fail(ND_ERR_ARG, "no such cluster plan for this size class");
     } else if (plan == kPlanGlobal) {
         if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
         if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
@@ -1342,7 +1351,7 @@ int nd_set_plan(nd_handle *h, int cls, int method, int plan)
         const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, plan);
         if (sm == (size_t)-1 || sm + 1024 > h->max_smem) return fail(ND_ERR_ARG, "variant does not fit in shared memory");
     } else if (plan != -1) {
-        return fail(ND_ERR_ARG, "plan must be -1, 0..2, 100 or 200");
+        return fail(ND_ERR_ARG, "plan must be -1, 0..2, 100, 200 or 201");
     }
     c.plan[method == ND_METHOD_RK4 ? 0 : 1] = plan;
     return ND_OK;
@@ -1356,7 +1365,7 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
     const SizeClass &c = h->classes[cls];
     auto threads = [&](int pl) {
         if (pl == kPlanGlobal) return 0;
-        if (pl == kPlanCluster) return 256 * 8;   // threads of the whole cluster
+        if (plan_cluster_nc(pl)) return 256 * plan_cluster_nc(pl);   // threads of the whole cluster
         if (!c.fused_main) return 0;
         return fused_variant_threads(c.P, pl < 0 ? 0 : pl);
     };

@@ -43,9 +43,10 @@ template <int P, typename T, int NC> struct ClusterGeom {
     static_assert(SPC >= 1 && (P / 2) % NC == 0, "column slots split evenly over the cluster");
     static_assert(3 * SPC <= NGRP, "one FFT group per (slot, component)");
     static constexpr int KH = SpecGeom<P>::KH;
-    // column buffer stride (rows y < D <= P/2): the groups of a half warp read
-    // columns that start on different banks
-    static constexpr int CY = P / 2 + (G == 4 ? 4 : 8);
+    // column buffer [3][P/2][SW]: row y of the CTA's SPC column slots, SW = SPC + 1
+    // words apart so that a group's column reads fall in different banks, and
+    // the lanes of a row group store neighbouring slots of one row
+    static constexpr int SW = SPC + 1;
     static constexpr int NTAB = SPC + 1;       // table slots: the CTA's columns, then kx = P/2
 };
 
@@ -58,7 +59,7 @@ __host__ __device__ __forceinline__ size_t cluster_smem_bytes(int D, int Dpad, b
     using CG = ClusterGeom<P, T, NC>;
     const int rpc = cluster_rows(D, NC);
     size_t b = sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G               // twiddles
-                                  + (size_t)3 * CG::SPC * CG::CY                        // column buffer
+                                  + (size_t)3 * (P / 2) * CG::SW                        // column buffer
                                   + (size_t)3 * rpc * SpecGeom<P>::RS                   // spectrum rows
                                   + (size_t)CG::NGRP * FFTGeom<P>::SCRATCH);            // FFT scratch
     b += sizeof(T) * (size_t)4 * CG::NTAB * CG::KH;                                     // kernel table
@@ -95,14 +96,14 @@ __device__ __forceinline__ void cluster_packed_scale(cplx<T> *v, const T *s0t, c
 }
 
 template <int P, typename T, int MODE, int NC>
-__global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 1)
     k_cluster(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
               const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base, int use_wbuf)
 {
     using Gm = FFTGeom<P>;
     using CG = ClusterGeom<P, T, NC>;
     constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, KH = CG::KH, NT = CG::NT, NGRP = CG::NGRP;
-    constexpr int SPC = CG::SPC, CY = CG::CY, NTAB = CG::NTAB;
+    constexpr int SPC = CG::SPC, SW = CG::SW, NTAB = CG::NTAB;
     static_assert(MODE == M_RK4 || MODE == M_HEUN, "stepping modes");
     cgc::cluster_group cluster = cgc::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -117,8 +118,8 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
     const long long lms = (long long)rpc * Dpad;                          // local state component stride
     const long long ms_s = (long long)D * Dpad;                           // global state component stride
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
-    cplx<T> *colbuf = tw + R1 * G;                                        // [3][SPC][CY]
-    cplx<T> *spec = colbuf + 3 * SPC * CY;                                // [3][rpc][RS]
+    cplx<T> *colbuf = tw + R1 * G;                                        // [3][P/2][SW]
+    cplx<T> *spec = colbuf + 3 * (P / 2) * SW;                            // [3][rpc][RS]
     cplx<T> *scratch = spec + 3 * lcs;
     T *gtab = reinterpret_cast<T *>(scratch + NGRP * Gm::SCRATCH);        // [4][NTAB][KH]
     T *msl = gtab + 4 * NTAB * KH;                                        // [3][rpc][Dpad]
@@ -212,13 +213,13 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                                 rB0 = B.x;
                             } else if (k == P / 2) {
                                 cplx<T> *dst = cluster.map_shared_rank(colbuf, 0);
-                                dst[(cA * SPC) * CY + yA] = {rA0, A.x};
-                                if (hasB) dst[(cB * SPC) * CY + yB] = {rB0, B.x};
+                                dst[(cA * (P / 2) + yA) * SW] = {rA0, A.x};
+                                if (hasB) dst[(cB * (P / 2) + yB) * SW] = {rB0, B.x};
                             } else {
                                 const int ow = k / SPC, j = k - ow * SPC;
                                 cplx<T> *dst = cluster.map_shared_rank(colbuf, ow);
-                                dst[(cA * SPC + j) * CY + yA] = A;
-                                if (hasB) dst[(cB * SPC + j) * CY + yB] = B;
+                                dst[(cA * (P / 2) + yA) * SW + j] = A;
+                                if (hasB) dst[(cB * (P / 2) + yB) * SW + j] = B;
                             }
                         }
                     }
@@ -233,11 +234,11 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
                 for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
                 const int kx = packed ? 0 : kslot;
                 if (ctask) {
-                    const cplx<T> *col = colbuf + (cc * SPC + cj) * CY;
+                    const cplx<T> *col = colbuf + cc * (P / 2) * SW + cj;
 #pragma unroll
                     for (int o = 0; o < R1 / 2; ++o) {
                         const int y = gid.t + G * o;
-                        if (y < D) v[o] = col[y];
+                        if (y < D) v[o] = col[y * SW];
                     }
                 }
                 // one transform call for both kinds of column, so that a warp
@@ -343,28 +344,67 @@ __global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256, 1)
     cluster.sync();   // no CTA leaves while another may still access its shared memory
 }
 
-// The cluster size of the on-chip sizes.
-constexpr int kClusterCTAs = 8;
-
-template <int P, typename T, int MODE>
-static cudaError_t launch_cluster_t(const LaunchArgs &a, int maxD, int maxDpad)
+// Launch configuration of one replica per cluster of NC CTAs (the cluster
+// shape is a launch attribute; NC = 16 is a non-portable size the GPU allows).
+template <int P, typename T, int MODE, int NC>
+static cudaError_t cluster_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int nwork, size_t sm,
+                                  cudaStream_t st)
 {
-    constexpr int NC = kClusterCTAs;
     auto kern = k_cluster<P, T, MODE, NC>;
-    const size_t sm = cluster_smem_bytes<P, T, NC>(maxD, maxDpad, a.use_wbuf != 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess && NC > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    kern<<<a.nwork * NC, ClusterGeom<P, T, NC>::NT, sm, a.stream>>>(a.reps, a.work, (T *)a.y,
-                                                                    (const cplx<T> *)a.tw, a.nsteps, a.step_base,
-                                                                    a.use_wbuf);
-    return cudaGetLastError();
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(nwork * NC, 1, 1);
+    cfg.blockDim = dim3(ClusterGeom<P, T, NC>::NT, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaSuccess;
 }
 
-template <int P, typename T>
+template <int P, typename T, int MODE, int NC>
+static cudaError_t launch_cluster_t(const LaunchArgs &a, int maxD, int maxDpad)
+{
+    const size_t sm = cluster_smem_bytes<P, T, NC>(maxD, maxDpad, a.use_wbuf != 0);
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = cluster_config<P, T, MODE, NC>(cfg, attr, a.nwork, sm, a.stream);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_cluster<P, T, MODE, NC>, a.reps, a.work, (T *)a.y, (const cplx<T> *)a.tw,
+                              a.nsteps, a.step_base, a.use_wbuf);
+}
+
+// Clusters of the size class that can be resident at once (0: the cluster
+// shape or its shared memory does not fit this GPU).
+template <int P, typename T, int NC>
+static int cluster_max_active_t(int maxD, int maxDpad, bool wbuf)
+{
+    const size_t sm = cluster_smem_bytes<P, T, NC>(maxD, maxDpad, wbuf);
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (cluster_config<P, T, M_HEUN, NC>(cfg, attr, 1, sm, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster<P, T, M_HEUN, NC>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int P, typename T, int NC>
 static cudaError_t launch_cluster_p(const LaunchArgs &a, int maxD, int maxDpad)
 {
-    if (a.mode == M_RK4) return launch_cluster_t<P, T, M_RK4>(a, maxD, maxDpad);
-    if (a.mode == M_HEUN) return launch_cluster_t<P, T, M_HEUN>(a, maxD, maxDpad);
+    if (a.mode == M_RK4) return launch_cluster_t<P, T, M_RK4, NC>(a, maxD, maxDpad);
+    if (a.mode == M_HEUN) return launch_cluster_t<P, T, M_HEUN, NC>(a, maxD, maxDpad);
     return cudaErrorInvalidValue;
 }
 

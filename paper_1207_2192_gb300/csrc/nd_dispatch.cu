@@ -18,10 +18,12 @@ cudaError_t launch_fused_f64(int P, const LaunchArgs &a);
 cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD);
 cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD);
 cudaError_t launch_relax_grad_f32(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
-size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf);
-size_t cluster_smem_f64(int P, int D, int Dpad, bool wbuf);
-cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad);
-cudaError_t launch_cluster_f64(int P, const LaunchArgs &a, int maxD, int maxDpad);
+size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf, int nc);
+size_t cluster_smem_f64(int P, int D, int Dpad, bool wbuf, int nc);
+int cluster_max_active_f32(int P, int D, int Dpad, bool wbuf, int nc);
+int cluster_max_active_f64(int P, int D, int Dpad, bool wbuf, int nc);
+cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad, int nc);
+cudaError_t launch_cluster_f64(int P, const LaunchArgs &a, int maxD, int maxDpad, int nc);
 cudaError_t launch_relax_grad_f64(const LaunchArgs &a, int maxD, const void *grad, const double *gscale);
 
 cudaError_t upload_twiddle_constants(const double *re, const double *im)
@@ -62,14 +64,21 @@ cudaError_t launch_relax_grad(int prec, const LaunchArgs &a, int maxD, const voi
     return prec == ND_PREC_FP64 ? launch_relax_grad_f64(a, maxD, grad, gscale) : launch_relax_grad_f32(a, maxD, grad, gscale);
 }
 
-size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf)
+size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf, int nc)
 {
-    return prec == ND_PREC_FP64 ? cluster_smem_f64(P, D, Dpad, wbuf) : cluster_smem_f32(P, D, Dpad, wbuf);
+    return prec == ND_PREC_FP64 ? cluster_smem_f64(P, D, Dpad, wbuf, nc) : cluster_smem_f32(P, D, Dpad, wbuf, nc);
 }
 
-cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad)
+int cluster_max_active(int P, int prec, int D, int Dpad, bool wbuf, int nc)
 {
-    return prec == ND_PREC_FP64 ? launch_cluster_f64(P, a, maxD, maxDpad) : launch_cluster_f32(P, a, maxD, maxDpad);
+    return prec == ND_PREC_FP64 ? cluster_max_active_f64(P, D, Dpad, wbuf, nc)
+                                : cluster_max_active_f32(P, D, Dpad, wbuf, nc);
+}
+
+cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad, int nc)
+{
+    return prec == ND_PREC_FP64 ? launch_cluster_f64(P, a, maxD, maxDpad, nc)
+                                : launch_cluster_f32(P, a, maxD, maxDpad, nc);
 }
 
 size_t spec_words(int P, int D)

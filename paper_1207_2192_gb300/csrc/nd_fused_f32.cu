@@ -54,26 +54,33 @@ cudaError_t launch_fused_f32(int P, const LaunchArgs &a)
     }
 }
 
-size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf)
+// Cluster plans: NC = 8 CTAs for every on-chip size, NC = 16 for P >= 32
+// (where the P/2 column slots split over 16 CTAs).
+#define ND_CLUSTER_CASES(X)      \
+    X(16, 8) X(32, 8) X(64, 8) X(128, 8) X(32, 16) X(64, 16) X(128, 16)
+
+size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf, int nc)
 {
-    switch (P) {
-    case 16: return cluster_smem_bytes<16, float, kClusterCTAs>(D, Dpad, wbuf);
-    case 32: return cluster_smem_bytes<32, float, kClusterCTAs>(D, Dpad, wbuf);
-    case 64: return cluster_smem_bytes<64, float, kClusterCTAs>(D, Dpad, wbuf);
-    case 128: return cluster_smem_bytes<128, float, kClusterCTAs>(D, Dpad, wbuf);
-    default: return (size_t)-1;
-    }
+#define X(p, n) if (P == p && nc == n) return cluster_smem_bytes<p, float, n>(D, Dpad, wbuf);
+    ND_CLUSTER_CASES(X)
+#undef X
+    return (size_t)-1;
 }
 
-cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad)
+int cluster_max_active_f32(int P, int D, int Dpad, bool wbuf, int nc)
 {
-    switch (P) {
-    case 16: return launch_cluster_p<16, float>(a, maxD, maxDpad);
-    case 32: return launch_cluster_p<32, float>(a, maxD, maxDpad);
-    case 64: return launch_cluster_p<64, float>(a, maxD, maxDpad);
-    case 128: return launch_cluster_p<128, float>(a, maxD, maxDpad);
-    default: return cudaErrorInvalidValue;
-    }
+#define X(p, n) if (P == p && nc == n) return cluster_max_active_t<p, float, n>(D, Dpad, wbuf);
+    ND_CLUSTER_CASES(X)
+#undef X
+    return 0;
+}
+
+cudaError_t launch_cluster_f32(int P, const LaunchArgs &a, int maxD, int maxDpad, int nc)
+{
+#define X(p, n) if (P == p && nc == n) return launch_cluster_p<p, float, n>(a, maxD, maxDpad);
+    ND_CLUSTER_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace nd

@@ -63,9 +63,10 @@ size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf = false, int varia
 int fused_blocks_per_sm(int P, int prec, int mode, size_t smem, int variant = 0);
 int fused_variant_threads(int P, int variant);   // 0 if the variant does not exist
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
-// One replica per thread-block cluster of 8 CTAs (P <= 128, stepping modes).
-size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf);   // (size_t)-1: no such size
-cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad);
+// One replica per thread-block cluster of nc = 8 or 16 CTAs (P <= 128, stepping modes).
+size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf, int nc);   // (size_t)-1: no such size
+int cluster_max_active(int P, int prec, int D, int Dpad, bool wbuf, int nc);  // 0: does not fit
+cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad, int nc);
 cudaError_t launch_global(int P, int prec, const LaunchArgs &a, int maxD);
 size_t spec_words(int P, int D);   // complex words of one replica's [3][D][RS] spectrum
 // One constrained-relaxation sweep over a size class with the field taken

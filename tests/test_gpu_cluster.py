@@ -1,6 +1,7 @@
-"""Single-disk stepping on a thread-block cluster (plan 200): each replica is
-spread over 8 CTAs whose shared memories hold its rows and exchange columns
-through distributed shared memory.  The per-element arithmetic is that of the
+"""Single-disk stepping on a thread-block cluster (plan 200: 8 CTAs, plan 201:
+16 CTAs for P >= 32): each replica is spread over the cluster's CTAs, whose
+shared memories hold its rows and exchange columns through distributed shared
+memory.  The per-element arithmetic is that of the
 one-CTA kernel, so trajectories match it, and they match the oracle's RK4 and
 stochastic Heun steps (Sec. II.C) to the field tolerance."""
 import numpy as np
@@ -13,15 +14,19 @@ from paper_1207_2192_gb300 import Disk, Nanodisk
 pytestmark = pytest.mark.gpu
 
 PLAN_CLUSTER = 200
+PLANS = [200, 201]
 DISKS = [Disk(6e-9, 3e-9, alpha=0.02), Disk(13e-9, 3e-9, alpha=0.02), Disk(24e-9, 5e-9, alpha=0.02),
          Disk(50e-9, 10e-9, alpha=0.02)]                    # P = 16, 32, 64, 128
 
 
-def cluster_handle(disks, reps, method, prec=nd.ND_FP32):
+def cluster_handle(disks, reps, method, prec=nd.ND_FP32, plan=PLAN_CLUSTER):
+    """A handle whose classes step on the cluster plan (the 16-CTA plan where
+    the class's P has one, else the 8-CTA plan)."""
     h = Nanodisk(disks, reps, prec)
     ci = 0
     while nd.nd_plan_info(h.h, ci) is not None:
-        nd.nd_set_plan(h.h, ci, method, PLAN_CLUSTER)
+        if nd.nd_set_plan(h.h, ci, method, plan, check=False) != nd.ND_OK:
+            nd.nd_set_plan(h.h, ci, method, PLAN_CLUSTER)
         ci += 1
     return h
 
@@ -37,16 +42,20 @@ def run(h, method, n, X0=None):
     return m
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("method", [nd.ND_METHOD_HEUN, nd.ND_METHOD_RK4])
-def test_cluster_plan_matches_one_cta_kernel(method):
+def test_cluster_plan_matches_one_cta_kernel(method, plan):
     reps = [3, 1, 2, 1]
     X0 = np.array([[1e-9 * (i % 3), -0.5e-9 * (i % 2)] for i in range(sum(reps))])
     ref = run(Nanodisk(DISKS, reps, nd.ND_FP32), method, 4, X0)
-    h = cluster_handle(DISKS, reps, method)
+    h = cluster_handle(DISKS, reps, method, plan=plan)
     info = [nd.nd_plan_info(h.h, ci) for ci in range(4)]
     key = "plan_heun" if method == nd.ND_METHOD_HEUN else "plan_rk4"
-    assert all(i[key] == PLAN_CLUSTER for i in info)
-    assert all(i["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] == 2048 for i in info)
+    want = [PLAN_CLUSTER] + [plan] * 3                      # P = 16 has only the 8-CTA plan
+    assert [i[key] for i in info] == want
+    nct = {200: 8, 201: 16}
+    assert [i["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] for i in info] == \
+        [256 * nct[p] for p in want]
     out = run(h, method, 4, X0)
     diff = (out - ref).abs().max().item()
     assert diff <= 1e-6, diff
@@ -64,21 +73,22 @@ def traj_ok(out, ref, start, model, prec):
     return np.linalg.norm((out - ref) * model.mask) <= 20 * TOL[prec] * change + floor
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("prec", [nd.ND_FP32, nd.ND_FP64])
 @pytest.mark.parametrize("R,L", [(13e-9, 3e-9), (24e-9, 5e-9), (50e-9, 10e-9)])
-def test_cluster_plan_matches_oracle(O, R, L, prec):
+def test_cluster_plan_matches_oracle(O, R, L, prec, plan):
     disk = Disk(R, L, alpha=0.02, hext=(2e3, -1e3, 5e2))
     model = O.Model(R, L, alpha=disk.alpha, hext=disk.hext)
     g = model.init_vortex(2e-9 if R > 20e-9 else 0.5e-9, -1e-9 if R > 20e-9 else 0.0)
     dt = 1e-14
-    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4, prec)
-    assert nd.nd_plan_info(h.h, 0)["plan_rk4"] == PLAN_CLUSTER
+    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4, prec, plan)
+    assert nd.nd_plan_info(h.h, 0)["plan_rk4"] == plan
     start = h.unpack(h.to_device([g]))[0]
     m = h.to_device([g])
     h.rk4(m, 3, dt)
     ref = model.rk4(start, 3, model.dtau(dt))
     assert traj_ok(h.unpack(m)[0], ref, start, model, prec)
-    h = cluster_handle([disk], [2], nd.ND_METHOD_HEUN, prec)
+    h = cluster_handle([disk], [2], nd.ND_METHOD_HEUN, prec, plan)
     m = h.to_device([g, g])
     h.heun(m, 3, dt, [300.0, 300.0], [21, 22], step0=5)
     Ts = O.scaled_temperature(300.0, disk.A, disk.L)
@@ -87,7 +97,8 @@ def test_cluster_plan_matches_oracle(O, R, L, prec):
         assert traj_ok(out, ref, start, model, prec)
 
 
-def test_cluster_plan_with_mask_and_field_schedule(O):
+@pytest.mark.parametrize("plan", PLANS)
+def test_cluster_plan_with_mask_and_field_schedule(O, plan):
     """An elliptical mask and a per-step field schedule on the cluster plan,
     against the oracle with the same mask and schedule."""
     disk = Disk(40e-9, 8e-9, alpha=0.05)
@@ -97,7 +108,7 @@ def test_cluster_plan_with_mask_and_field_schedule(O):
     c = 0.5 * (D - 1)
     mask = (((xx - c) / (0.5 * D)) ** 2 + ((yy - c) / (0.35 * D)) ** 2 <= 1.0).astype(np.uint8)
     sched = np.array([[1e4 * np.sin(0.3 * k), 5e3, -2e3] for k in range(6)])
-    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4)
+    h = cluster_handle([disk], [1], nd.ND_METHOD_RK4, plan=plan)
     h.set_mask(0, mask)
     h.set_field_schedule(0, sched)
     model.set_mask(mask)
@@ -114,6 +125,9 @@ def test_cluster_plan_is_offered_by_autotune():
     h = Nanodisk([Disk(50e-9, 10e-9, alpha=0.02)], [1], nd.ND_FP32)
     assert nd.nd_set_plan(h.h, 0, nd.ND_METHOD_HEUN, PLAN_CLUSTER, check=False) == nd.ND_OK
     big = Nanodisk([Disk(200e-9, 10e-9)], [1], nd.ND_FP32)            # P = 512: no cluster plan
-    assert nd.nd_set_plan(big.h, 0, nd.ND_METHOD_HEUN, PLAN_CLUSTER, check=False) == nd.ND_ERR_ARG
+    for plan in PLANS:
+        assert nd.nd_set_plan(big.h, 0, nd.ND_METHOD_HEUN, plan, check=False) == nd.ND_ERR_ARG
+    tiny = Nanodisk([Disk(6e-9, 3e-9)], [1], nd.ND_FP32)               # P = 16: 8 CTAs only
+    assert nd.nd_set_plan(tiny.h, 0, nd.ND_METHOD_HEUN, 201, check=False) == nd.ND_ERR_ARG
     nd.nd_autotune(h.h, nd.ND_METHOD_HEUN, 1e-14, 5)
-    assert nd.nd_plan_info(h.h, 0)["plan_heun"] in (0, 1, 2, 100, PLAN_CLUSTER)
+    assert nd.nd_plan_info(h.h, 0)["plan_heun"] in (0, 1, 2, 100, 200, 201)
