@@ -180,7 +180,7 @@ class Workload:
         self.h = nd.Nanodisk([self.disk], [self.B], nd.ND_FP32)
         # the stepping plan of the size class: the public autotuner times the
         # one-CTA kernel's thread counts, the cluster plan and the global path
-        nd.nd_autotune(self.h.h, nd.ND_METHOD_HEUN, DT, 10)
+        nd.nd_autotune(self.h.h, nd.ND_METHOD_HEUN, DT, CHUNK)
         L0 = self.h.layout[0]
         self.D, self.P, self.C = L0["D"], L0["P"], L0["cells"]
         self.m = self.h.empty_device()
