@@ -251,7 +251,7 @@ def kernel_name(wl):
     path)."""
     info = wl.nd.nd_plan_info(wl.h.h, 0)
     if info and info["plan_heun"] in (200, 201):
-        nc = info["threads_heun"] // 256
+        nc = info["threads_heun"] // (512 if wl.P >= 256 else 256)
         return f"k_cluster<{wl.P},float,HEUN,{nc}> (one replica per {nc}-CTA cluster)"
     if info and info["threads_heun"] > 0:
         return f"k_fused<{wl.P},float,HEUN,{info['threads_heun']}>"

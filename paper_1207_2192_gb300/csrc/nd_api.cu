@@ -1371,7 +1371,7 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
     const SizeClass &c = h->classes[cls];
     auto threads = [&](int pl) {
         if (pl == kPlanGlobal) return 0;
-        if (plan_cluster_nc(pl)) return 256 * plan_cluster_nc(pl);   // threads of the whole cluster
+        if (plan_cluster_nc(pl)) return cluster_cta_threads(c.P) * plan_cluster_nc(pl);   // threads of the cluster
         if (!c.fused_main) return 0;
         return fused_variant_threads(c.P, pl < 0 ? 0 : pl);
     };

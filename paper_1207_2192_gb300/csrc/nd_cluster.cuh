@@ -1,6 +1,7 @@
 // nd_cluster.cuh -- one replica's time steps on a thread-block cluster of NC
-// CTAs (one per SM), for the on-chip sizes P <= 128 when a class has too few
-// replicas to fill the GPU with one CTA each.
+// CTAs (one per SM): for the sizes P <= 128 when a class has too few replicas
+// to fill the GPU with one CTA each, and for P = 256, whose spectrum fits in
+// the shared memory of 16 CTAs but not of one.
 //
 // The replica's rows are split over the cluster: CTA k owns rows
 // [k rpc, (k+1) rpc) of the disk (rpc even, so z row pairs stay whole) and
@@ -37,7 +38,8 @@ namespace cgc = cooperative_groups;
 
 template <int P, typename T, int NC> struct ClusterGeom {
     static constexpr int G = FFTGeom<P>::G;
-    static constexpr int NT = 256;
+    // threads per CTA: enough FFT groups for one per (column slot, component)
+    static constexpr int NT = cluster_cta_threads(P);
     static constexpr int NGRP = NT / G;
     static constexpr int SPC = (P / 2) / NC;   // column slots per CTA
     static_assert(SPC >= 1 && (P / 2) % NC == 0, "column slots split evenly over the cluster");
@@ -96,7 +98,7 @@ __device__ __forceinline__ void cluster_packed_scale(cplx<T> *v, const T *s0t, c
 }
 
 template <int P, typename T, int MODE, int NC>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
     k_cluster(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
               const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base, int use_wbuf)
 {

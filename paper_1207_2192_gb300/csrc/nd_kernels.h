@@ -63,7 +63,9 @@ size_t fused_smem(int P, int prec, int D, int Dpad, bool wbuf = false, int varia
 int fused_blocks_per_sm(int P, int prec, int mode, size_t smem, int variant = 0);
 int fused_variant_threads(int P, int variant);   // 0 if the variant does not exist
 cudaError_t launch_fused(int P, int prec, const LaunchArgs &a);
-// One replica per thread-block cluster of nc = 8 or 16 CTAs (P <= 128, stepping modes).
+// One replica per thread-block cluster of nc = 8 or 16 CTAs (P <= 128; P = 256
+// on 16 CTAs; stepping modes), of cluster_cta_threads(P) threads per CTA.
+constexpr int cluster_cta_threads(int P) { return P >= 256 ? 512 : 256; }
 size_t cluster_smem(int P, int prec, int D, int Dpad, bool wbuf, int nc);   // (size_t)-1: no such size
 int cluster_max_active(int P, int prec, int D, int Dpad, bool wbuf, int nc);  // 0: does not fit
 cudaError_t launch_cluster(int P, int prec, const LaunchArgs &a, int maxD, int maxDpad, int nc);

@@ -131,3 +131,33 @@ def test_cluster_plan_is_offered_by_autotune():
     assert nd.nd_set_plan(tiny.h, 0, nd.ND_METHOD_HEUN, 201, check=False) == nd.ND_ERR_ARG
     nd.nd_autotune(h.h, nd.ND_METHOD_HEUN, 1e-14, 5)
     assert nd.nd_plan_info(h.h, 0)["plan_heun"] in (0, 1, 2, 100, 200, 201)
+
+
+@pytest.mark.parametrize("method", [nd.ND_METHOD_HEUN, nd.ND_METHOD_RK4])
+def test_p256_cluster_plan_matches_global_path_and_oracle(O, method):
+    """P = 256 (D = 70): the spectrum of one replica is too large for one
+    CTA's shared memory but fits in a 16-CTA cluster's; against the global
+    path (plan 100) and the oracle."""
+    disk = Disk(70e-9, 10e-9, alpha=0.02, hext=(1e3, 0.0, -2e3))
+    h = Nanodisk([disk], [2], nd.ND_FP32)
+    assert h.layout[0]["P"] == 256
+    assert nd.nd_set_plan(h.h, 0, method, 200, check=False) == nd.ND_ERR_ARG      # 8 CTAs: no such plan
+    nd.nd_set_plan(h.h, 0, method, 201)
+    assert nd.nd_plan_info(h.h, 0)["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] == 16 * 512
+    hg = Nanodisk([disk], [2], nd.ND_FP32)
+    nd.nd_set_plan(hg.h, 0, method, 100)
+    X0 = np.array([[3e-9, 1e-9], [-2e-9, 0.0]])
+    out, ref = run(h, method, 3, X0), run(hg, method, 3, X0)
+    assert (out - ref).abs().max().item() <= 1e-6
+    model = O.Model(disk.R, disk.L, alpha=disk.alpha, hext=disk.hext)
+    start = h.unpack(h.to_device([model.init_vortex(3e-9, 1e-9)]))[0]
+    m = h.to_device([start, start])
+    if method == nd.ND_METHOD_RK4:
+        h.rk4(m, 2, 1e-14)
+        refs = [model.rk4(start, 2, model.dtau(1e-14))] * 2
+    else:
+        h.heun(m, 2, 1e-14, [300.0, 300.0], [5, 6], step0=3)
+        Ts = O.scaled_temperature(300.0, disk.A, disk.L)
+        refs = [model.heun(start, 2, model.dtau(1e-14), Ts, s, 3) for s in (5, 6)]
+    for o, r in zip(h.unpack(m), refs):
+        assert traj_ok(o, r, start, model, nd.ND_FP32)
