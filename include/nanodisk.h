@@ -283,6 +283,20 @@ int nd_stats_sample(nd_handle *h, const void *m, double dt_sample_seconds, void 
 int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, unsigned long long *v_hist,
                   void *stream);
 
+/* Checkpoint of the statistics accumulators, so that a run split over
+ * processes accumulates exactly as one uninterrupted run (the noise stream
+ * resumes from the step counter, nd_step_heun's step0).  nd_stats_save_bytes
+ * gives the size of the record; nd_stats_save synchronises `stream` and
+ * writes, into the caller's host buffer of that size, the histogram ranges,
+ * every replica's sums and the previous core position that continues its
+ * speed chain, and both histograms.  nd_stats_load checks the record (a
+ * leading tag, the replica count of the handle) and restores it, allocating
+ * as nd_stats_reset does.  ND_ERR_ARG for a null buffer, a short buffer, a
+ * record of another replica count, or (save) a handle without statistics. */
+size_t nd_stats_save_bytes(const nd_handle *h);
+int nd_stats_save(nd_handle *h, void *buf, size_t bytes, void *stream);
+int nd_stats_load(nd_handle *h, const void *buf, size_t bytes, void *stream);
+
 /* Average magnetisation <m> = (1/N) sum_i m_i over each disk (Sec. IV);
  * out is a host array [B][3].  Synchronises `stream`. */
 int nd_mean_m(nd_handle *h, const void *m, double *out, void *stream);

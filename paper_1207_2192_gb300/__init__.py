@@ -19,13 +19,14 @@ from ._binding import (ND_METHOD_HEUN, ND_METHOD_RK4, nd_autotune, nd_plan_info,
                        nd_effective_field, nd_energy, nd_get_info, nd_init_vortex, nd_last_error, nd_mean_m,
                        nd_relax_constrained, nd_replica_layout, nd_set_damping, nd_set_green_tensor, nd_step_heun,
                        nd_set_mask, nd_set_field_schedule,
-                       nd_stats_read, nd_stats_reset, nd_stats_sample, nd_step_rk4, nd_units, nd_vortex_core)
+                       nd_stats_read, nd_stats_reset, nd_stats_sample, nd_stats_save, nd_stats_load, nd_step_rk4, nd_units,
+                       nd_vortex_core)
 
 __all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "ND_GRID_3X", "nd_create_disk", "nd_destroy", "nd_effective_field",
            "nd_energy", "nd_step_rk4", "nd_step_heun", "nd_init_vortex", "nd_vortex_core", "nd_mean_m",
            "nd_set_green_tensor", "nd_set_damping", "nd_set_mask", "nd_set_field_schedule", "nd_units", "nd_replica_layout", "nd_get_info",
            "nd_disk_mask", "nd_last_error", "nd_relax_constrained",
-           "nd_stats_reset", "nd_stats_sample", "nd_stats_read", "nd_check_status", "nd_selftest_handover_timeout",
+           "nd_stats_reset", "nd_stats_sample", "nd_stats_read", "nd_stats_save", "nd_stats_load", "nd_check_status", "nd_selftest_handover_timeout",
            "nd_series_reset", "nd_series_sample", "nd_series_read", "nd_power_spectrum", "ND_GRAPH_STATS", "ND_GRAPH_SERIES",
            "nd_graph_create", "nd_graph_launch", "nd_graph_nodes", "nd_graph_destroy",
            "nd_autotune", "nd_plan_info", "nd_set_plan"]

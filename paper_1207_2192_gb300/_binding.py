@@ -80,6 +80,9 @@ SIGNATURES = {
     "nd_series_read": (_I, [_P, _P, _P]),
     "nd_power_spectrum": (_I, [_P, _I, _I, _D, _P, _P, _P, _P]),
     "nd_stats_read": (_I, [_P, _P, _P, _P, _P]),
+    "nd_stats_save_bytes": (ctypes.c_size_t, [_P]),
+    "nd_stats_save": (_I, [_P, _P, ctypes.c_size_t, _P]),
+    "nd_stats_load": (_I, [_P, _P, ctypes.c_size_t, _P]),
     "nd_step_heun_noalloc": (_I, [_P, _I, _P, _LL, _D, _P, _P, _ULL, _P]),
 }
 
@@ -295,6 +298,21 @@ def nd_stats_read(h, nrep, r_bins, v_bins, stream=None):
     hv = np.zeros((nrep, v_bins), dtype=np.uint64)
     _check(lib().nd_stats_read(h, _ptr(mom), _ptr(hr), _ptr(hv), _stream(stream)))
     return mom, hr, hv
+
+
+def nd_stats_save(h, stream=None):
+    """The statistics accumulators as a bytes record (nd_stats_load restores it)."""
+    n = lib().nd_stats_save_bytes(h)
+    if n == 0:
+        raise NDError(ND_ERR_ARG, "no statistics to save")
+    buf = ctypes.create_string_buffer(n)
+    _check(lib().nd_stats_save(h, buf, n, _stream(stream)))
+    return buf.raw
+
+
+def nd_stats_load(h, record, stream=None):
+    buf = ctypes.create_string_buffer(bytes(record), len(record))
+    _check(lib().nd_stats_load(h, buf, len(record), _stream(stream)))
 
 
 def nd_series_reset(h, capacity):

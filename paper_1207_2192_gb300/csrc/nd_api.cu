@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <string>
 #include <vector>
@@ -1149,6 +1150,83 @@ int nd_stats_read(nd_handle *h, double *moments, unsigned long long *r_hist, uns
         }
     if (r_hist) ND_CUDA(cudaMemcpy(r_hist, h->hist_r, sizeof(unsigned long long) * B * h->rbins, cudaMemcpyDeviceToHost));
     if (v_hist) ND_CUDA(cudaMemcpy(v_hist, h->hist_v, sizeof(unsigned long long) * B * h->vbins, cudaMemcpyDeviceToHost));
+    return ND_OK;
+}
+
+// Statistics record: tag, replica count, bin counts, ranges, then per replica
+// the StatsAcc fields as doubles (have_prev as 0/1), then both histograms.
+namespace {
+constexpr unsigned long long kStatsTag = 0x3154535344444e4eull;   // "NNDDSST1"
+constexpr int kStatsWords = 10;                                   // doubles per replica
+}
+
+size_t nd_stats_save_bytes(const nd_handle *h)
+{
+    if (!h || !h->stats) return 0;
+    const size_t B = h->rep_disk.size();
+    return sizeof(unsigned long long) * 4 + sizeof(double) * 2 + sizeof(double) * kStatsWords * B +
+           sizeof(unsigned long long) * B * (size_t)(h->rbins + h->vbins);
+}
+
+int nd_stats_save(nd_handle *h, void *buf, size_t bytes, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!h->stats) return fail(ND_ERR_ARG, "no statistics to save (nd_stats_reset first)");
+    if (!buf || bytes < nd_stats_save_bytes(h)) return fail(ND_ERR_ARG, "statistics record buffer too small");
+    const int B = (int)h->rep_disk.size();
+    ND_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<StatsAcc> s(B);
+    ND_CUDA(cudaMemcpy(s.data(), h->stats, sizeof(StatsAcc) * B, cudaMemcpyDeviceToHost));
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    const unsigned long long head[4] = {kStatsTag, (unsigned long long)B, (unsigned long long)h->rbins,
+                                        (unsigned long long)h->vbins};
+    std::memcpy(p, head, sizeof(head)); p += sizeof(head);
+    const double range[2] = {h->r_max, h->v_max};
+    std::memcpy(p, range, sizeof(range)); p += sizeof(range);
+    for (int r = 0; r < B; ++r) {
+        const double w[kStatsWords] = {s[r].n, s[r].sx, s[r].sy, s[r].sr2, s[r].nv, s[r].sv2, s[r].no_vortex,
+                                       s[r].px, s[r].py, s[r].have_prev ? 1.0 : 0.0};
+        std::memcpy(p, w, sizeof(w)); p += sizeof(w);
+    }
+    ND_CUDA(cudaMemcpy(p, h->hist_r, sizeof(unsigned long long) * B * h->rbins, cudaMemcpyDeviceToHost));
+    p += sizeof(unsigned long long) * B * h->rbins;
+    ND_CUDA(cudaMemcpy(p, h->hist_v, sizeof(unsigned long long) * B * h->vbins, cudaMemcpyDeviceToHost));
+    return ND_OK;
+}
+
+int nd_stats_load(nd_handle *h, const void *buf, size_t bytes, void *stream)
+{
+    if (int rc = check_handle(h)) return rc;
+    const size_t hb = sizeof(unsigned long long) * 4 + sizeof(double) * 2;
+    if (!buf || bytes < hb) return fail(ND_ERR_ARG, "statistics record too short");
+    const unsigned char *p = static_cast<const unsigned char *>(buf);
+    unsigned long long head[4];
+    double range[2];
+    std::memcpy(head, p, sizeof(head));
+    std::memcpy(range, p + sizeof(head), sizeof(range));
+    const int B = (int)h->rep_disk.size();
+    if (head[0] != kStatsTag) return fail(ND_ERR_ARG, "not a statistics record");
+    if (head[1] != (unsigned long long)B) return fail(ND_ERR_ARG, "statistics record of another replica count");
+    if (head[2] < 1 || head[3] < 1 || head[2] > (1u << 24) || head[3] > (1u << 24))
+        return fail(ND_ERR_ARG, "bad histogram sizes in the statistics record");
+    const int rb = (int)head[2], vb = (int)head[3];
+    const size_t need = hb + sizeof(double) * kStatsWords * B + sizeof(unsigned long long) * B * (size_t)(rb + vb);
+    if (bytes < need) return fail(ND_ERR_ARG, "statistics record too short");
+    ND_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (int rc = nd_stats_reset(h, range[0], rb, range[1], vb)) return rc;
+    p += hb;
+    std::vector<StatsAcc> s(B);
+    for (int r = 0; r < B; ++r) {
+        double w[kStatsWords];
+        std::memcpy(w, p, sizeof(w)); p += sizeof(w);
+        s[r] = StatsAcc{};
+        s[r].n = w[0]; s[r].sx = w[1]; s[r].sy = w[2]; s[r].sr2 = w[3]; s[r].nv = w[4]; s[r].sv2 = w[5];
+        s[r].no_vortex = w[6]; s[r].px = w[7]; s[r].py = w[8]; s[r].have_prev = w[9] != 0.0;
+    }
+    ND_CUDA(cudaMemcpy(h->stats, s.data(), sizeof(StatsAcc) * B, cudaMemcpyHostToDevice));
+    ND_CUDA(cudaMemcpy(h->hist_r, p, sizeof(unsigned long long) * B * rb, cudaMemcpyHostToDevice));
+    p += sizeof(unsigned long long) * B * rb;
+    ND_CUDA(cudaMemcpy(h->hist_v, p, sizeof(unsigned long long) * B * vb, cudaMemcpyHostToDevice));
     return ND_OK;
 }
 
