@@ -371,14 +371,25 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
  * trajectories are bit-identical).  The graph keeps its own copy of the
  * per-replica parameters (dt, T, seeds, damping at creation time) and works
  * on the buffer m given at creation.  Uneven multi-disk handles become one
- * graph with a launch per FFT size class.  The paper has no counterpart
- * (it is the batching of Sec. III's integrators).  nd_graph_nodes reports
- * the number of kernel nodes of one replay. */
+ * graph with a launch per FFT size class; the classes' launches are
+ * independent branches of the graph (and, outside graphs, run on side streams
+ * of the handle) so that they share the GPU, unless a class has more replicas
+ * than the GPU has SMs.  The paper has no counterpart (it is the batching of
+ * Sec. III's integrators).  nd_graph_nodes reports the number of kernel nodes
+ * of one replay, counting those inside joined graphs.
+ *
+ * nd_graph_join makes one graph of n_parts graphs (for example the RK4 graph
+ * of a handle of T = 0 replicas and the Heun graph of a handle of the others)
+ * as independent branches: one nd_graph_launch replays all parts side by
+ * side, each advancing its own step counter as its own launch would.  The
+ * parts must outlive the joined graph (it uses their device buffers); destroy
+ * it with nd_graph_destroy.  ND_ERR_ARG for no parts or a null part. */
 typedef struct nd_graph nd_graph;
 #define ND_GRAPH_STATS 1
 #define ND_GRAPH_SERIES 2
 int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double dt_seconds, const double *T_kelvin,
                     const unsigned long long *seed, unsigned long long step0, int stats_sample, nd_graph **out);
+int nd_graph_join(nd_graph *const *parts, int n_parts, nd_graph **out);
 int nd_graph_launch(nd_graph *g, void *stream);
 int nd_graph_nodes(const nd_graph *g, int *n_kernel_nodes);
 void nd_graph_destroy(nd_graph *g);

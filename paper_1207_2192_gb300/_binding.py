@@ -72,6 +72,7 @@ SIGNATURES = {
     "nd_set_plan": (_I, [_P, _I, _I, _I]),
     "nd_plan_info": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "nd_graph_launch": (_I, [_P, _P]),
+    "nd_graph_join": (_I, [_P, _I, _P]),
     "nd_graph_nodes": (_I, [_P, _P]),
     "nd_graph_destroy": (None, [_P]),
     "nd_stats_sample": (_I, [_P, _P, _D, _P]),
@@ -366,6 +367,14 @@ def nd_graph_create(h, m, method, n_steps, dt_seconds, T_kelvin=None, seed=None,
     g = ctypes.c_void_p()
     _check(lib().nd_graph_create(h, _ptr(m), method, n_steps, dt_seconds, _ptr(T), _ptr(s), step0, int(stats_sample),
                                  ctypes.byref(g)))
+    return g.value
+
+
+def nd_graph_join(parts):
+    """One graph replaying the given graphs side by side (the parts must outlive it)."""
+    arr = (ctypes.c_void_p * len(parts))(*parts)
+    g = ctypes.c_void_p()
+    _check(lib().nd_graph_join(ctypes.cast(arr, _P), len(parts), ctypes.byref(g)))
     return g.value
 
 

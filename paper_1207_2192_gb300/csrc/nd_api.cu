@@ -165,6 +165,11 @@ struct nd_handle {
     double *a_rep = nullptr;              // [B] cell edge per replica
     size_t max_smem = 0;
     int n_sm = 0;
+    // side streams and fork/join events: the stepping kernels of different
+    // size classes run side by side (class 0 on the caller's stream)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr;
     int *flags_d = nullptr;               // [B] replica hand-over flags of the time-sliced schedule
     unsigned *status_d = nullptr;         // device status word (ND_DEV_* bits)
     unsigned long long rk4_step = 0;      // step index of the next nd_step_rk4 step (field schedules)
@@ -279,9 +284,25 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
                     const Replica *reps = nullptr, int only_class = -1)
 {
     const int prec = fp64 ? ND_PREC_FP64 : (h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32);
+    // The stepping kernels of the size classes are independent (each touches
+    // only its replicas' state and scratch), so they run side by side on
+    // forked streams: a class fills only the SMs of its replicas.  Not when a
+    // class needs the time-sliced schedule, whose cooperative launch takes the
+    // whole GPU.
+    bool concurrent = (mode == M_RK4 || mode == M_HEUN) && only_class < 0 && h->classes.size() > 1 &&
+                      h->side.size() + 1 == h->classes.size();
+    for (const auto &c : h->classes)
+        if ((int)c.reps.size() > h->n_sm) concurrent = false;
+    if (concurrent) ND_CUDA(cudaEventRecord(h->fork_ev, st));
+    const cudaStream_t st0 = st;
     for (int ci = 0; ci < (int)h->classes.size(); ++ci) {
         if (only_class >= 0 && ci != only_class) continue;
         auto &c = h->classes[ci];
+        cudaStream_t st = st0;
+        if (concurrent && ci > 0) {
+            st = h->side[ci - 1];
+            ND_CUDA(cudaStreamWaitEvent(st, h->fork_ev, 0));
+        }
         LaunchArgs a;
         a.mode = mode;
         a.reps = reps ? reps : h->reps_d;
@@ -362,7 +383,10 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         // a stepped state with a non-finite cell sets the NaN bit of the status word
         if (mode == M_RK4 || mode == M_HEUN)
             ND_CUDA(launch_check_finite(prec, a.reps, c.work_d, (int)c.reps.size(), c.maxD, y, h->status_d, st));
+        if (concurrent && ci > 0) ND_CUDA(cudaEventRecord(h->join_ev[ci - 1], st));
     }
+    if (concurrent)
+        for (size_t k = 0; k < h->side.size(); ++k) ND_CUDA(cudaStreamWaitEvent(st0, h->join_ev[k], 0));
     return ND_OK;
 }
 
@@ -504,6 +528,18 @@ int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_p
     }
     int rc = setup_class_paths(h);
     if (rc) { nd_destroy(h); return rc; }
+    if (h->classes.size() > 1) {
+        bool ok = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (size_t k = 1; ok && k < h->classes.size(); ++k) {
+            cudaStream_t s2 = nullptr;
+            cudaEvent_t e2 = nullptr;
+            ok = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) == cudaSuccess;
+            if (s2) h->side.push_back(s2);
+            if (e2) h->join_ev.push_back(e2);
+        }
+        if (!ok) { nd_destroy(h); return fail(ND_ERR_CUDA, "side streams for the size classes"); }
+    }
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         std::string m = std::string(what) + ": " + cudaGetErrorString(e);
         nd_destroy(h);
@@ -593,6 +629,9 @@ void nd_destroy(nd_handle *h)
         cudaFree(d.mask_d); cudaFree(d.cells_d); cudaFree(d.ghat64); cudaFree(d.ghat32); cudaFree(d.ghatL);
         cudaFree(d.sched32); cudaFree(d.sched64);
     }
+    for (auto st2 : h->side) { cudaStreamSynchronize(st2); cudaStreamDestroy(st2); }
+    for (auto e2 : h->join_ev) cudaEventDestroy(e2);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     for (auto &c : h->classes) { cudaFree(c.work_d); cudaFree(c.segs_d); cudaFree(c.seg_off_d); }
     cudaFree(h->flags_d);
     cudaFree(h->status_d);
@@ -1462,6 +1501,28 @@ int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan
     return ND_OK;
 }
 
+// Kernel nodes of a graph, counting those inside child graphs.
+static cudaError_t count_kernel_nodes(cudaGraph_t graph, int *count)
+{
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(graph, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if ((e = cudaGraphGetNodes(graph, nodes.data(), &n)) != cudaSuccess) return e;
+    for (auto node : nodes) {
+        cudaGraphNodeType t;
+        if ((e = cudaGraphNodeGetType(node, &t)) != cudaSuccess) return e;
+        if (t == cudaGraphNodeTypeKernel) {
+            ++*count;
+        } else if (t == cudaGraphNodeTypeGraph) {
+            cudaGraph_t child = nullptr;
+            if ((e = cudaGraphChildGraphNodeGetGraph(node, &child)) != cudaSuccess) return e;
+            if ((e = count_kernel_nodes(child, count)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 struct nd_graph {
     nd_handle *h = nullptr;
     Replica *reps = nullptr;          // private parameter blocks (step counter advanced on the device)
@@ -1542,6 +1603,28 @@ int nd_graph_create(nd_handle *h, void *m, int method, long long n_steps, double
     return ND_OK;
 }
 
+int nd_graph_join(nd_graph *const *parts, int n_parts, nd_graph **out)
+{
+    if (!out) return fail(ND_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!parts || n_parts < 1) return fail(ND_ERR_ARG, "no graphs to join");
+    for (int k = 0; k < n_parts; ++k)
+        if (!parts[k] || !parts[k]->graph) return fail(ND_ERR_ARG, "null graph among the parts");
+    nd_graph *g = new nd_graph();
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    for (int k = 0; k < n_parts && e == cudaSuccess; ++k) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, g->graph, nullptr, 0, parts[k]->graph);   // no edges: side by side
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        nd_graph_destroy(g);
+        return fail(ND_ERR_CUDA, std::string("graph join: ") + cudaGetErrorString(e));
+    }
+    *out = g;
+    return ND_OK;
+}
+
 int nd_graph_launch(nd_graph *g, void *stream)
 {
     if (!g || !g->exec) return fail(ND_ERR_ARG, "null graph");
@@ -1552,15 +1635,8 @@ int nd_graph_launch(nd_graph *g, void *stream)
 int nd_graph_nodes(const nd_graph *g, int *n_kernel_nodes)
 {
     if (!g || !g->graph || !n_kernel_nodes) return fail(ND_ERR_ARG, "null argument");
-    size_t n = 0;
-    ND_CUDA(cudaGraphGetNodes(g->graph, nullptr, &n));
-    std::vector<cudaGraphNode_t> nodes(n);
-    ND_CUDA(cudaGraphGetNodes(g->graph, nodes.data(), &n));
     int k = 0;
-    for (auto nd_ : nodes) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd_, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
-    }
+    ND_CUDA(count_kernel_nodes(g->graph, &k));
     *n_kernel_nodes = k;
     return ND_OK;
 }
