@@ -1414,6 +1414,12 @@ int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // With several size classes the classes step side by side and share the
+    // GPU, so each candidate is timed on the whole handle with the other
+    // classes at their current plans (one pass of coordinate descent), not on
+    // its class alone: a plan that is fastest alone (a cluster plan spreading
+    // few replicas over many SMs) can take SMs the other classes need.
+    const int only = h->classes.size() > 1 ? -1 : 0;
     for (int ci = 0; ci < (int)h->classes.size() && rc == ND_OK; ++ci) {
         SizeClass &c = h->classes[ci];
         std::vector<int> cands;
@@ -1431,13 +1437,14 @@ int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, 
             c.plan[slot] = cand;
             fill_reps(h, h->prec == ND_FP64, dt_seconds, mode == M_HEUN ? T.data() : nullptr, mode == M_HEUN ? sd.data() : nullptr, 0);
             upload_reps(h, st);
-            rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, ci);   // warm-up, builds schedules
+            const int which = only < 0 ? -1 : ci;
+            rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, which);   // warm-up, builds schedules
             if (rc) break;
             // the fastest of three timed runs: one run is at the mercy of clock ramps and neighbours
             float ms = 1e30f;
             for (int rep = 0; rep < 3 && rc == ND_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, ci);
+                rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, which);
                 cudaEventRecord(e1, st);
                 if (rc) break;
                 cudaEventSynchronize(e1);
