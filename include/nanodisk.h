@@ -418,7 +418,9 @@ void nd_graph_destroy(nd_graph *g);
  * device pointer on the current device (a buffer of another GPU is rejected).
  *
  * The first call on a device resolves the array's address on that device and
- * loads the FFT constants; make that first call before any stream capture.
+ * loads the FFT constants.  The call cannot be stream-captured (its parameter
+ * blocks go up from one static host array, which a replay would not refresh):
+ * on a capturing stream it returns ND_ERR_ARG before issuing any work.
  * A call with a new geometry rebuilds the spectral kernel and synchronises
  * `stream`.  Every call shares the array and leaves its contents behind, so
  * calls whose work overlaps on the GPU (other streams, other threads) race.

@@ -138,6 +138,18 @@ extern "C" int nd_step_heun_noalloc(const nd_disk_desc *disk, int n_replicas, fl
 
     std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        // the parameter blocks go up from one static host array, so a captured
+        // call would replay whatever the last call left there, not its own T,
+        // seeds and step0
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ND_ERR_CUDA, "nd_step_heun_noalloc: cannot query the stream's capture status");
+        }
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(ND_ERR_ARG, "nd_step_heun_noalloc: the stream is being captured; this call cannot be captured");
+    }
     DeviceSlot &S = g_slots[dev];
     if (!S.ready) {
         // once per device, with the device current: resolve the array's device address

@@ -76,3 +76,31 @@ def test_noalloc_rejects_what_exceeds_its_limits():
     host = np.zeros(3 * 30 * 32, dtype=np.float32)
     assert _binding.nd_step_heun_noalloc(small, 1, host, 1, 1e-14, T, s, check=False) == nd.ND_ERR_ARG
     assert "device pointer" in nd.nd_last_error()
+
+
+def test_noalloc_refuses_stream_capture():
+    """A captured call would replay stale parameter blocks, so it is refused
+    on a capturing stream before any work is issued; the capture stays valid
+    and an ordinary call afterwards steps as before."""
+    import torch
+    disk = Disk(30e-9, 5e-9, alpha=0.02)
+    h = Nanodisk([disk], [1], nd.ND_FP32)
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((1, 2)))
+    T, s = np.full(1, 300.0), np.arange(1, dtype=np.uint64)
+    _binding.nd_step_heun_noalloc(disk, 1, m, 1, 1e-14, T, s)           # first call outside any capture
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    scratch = torch.zeros(4, device="cuda")
+    with torch.cuda.graph(g, stream=side):
+        rc = _binding.nd_step_heun_noalloc(disk, 1, m, 1, 1e-14, T, s, stream=side, check=False)
+        scratch.add_(1.0)                                                  # the capture itself goes on
+    assert rc == nd.ND_ERR_ARG and "captured" in nd.nd_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(scratch, torch.ones(4, device="cuda"))
+    before = m.clone()
+    assert _binding.nd_step_heun_noalloc(disk, 1, m, 1, 1e-14, T, s, step0=1) == nd.ND_OK
+    torch.cuda.synchronize()
+    assert not torch.equal(before, m)
