@@ -330,6 +330,7 @@ static int run_mode(nd_handle *h, int mode, bool fp64, void *y, void *out, long 
         if (mode == M_RK4 || mode == M_HEUN) a.acc = h->acc;
         if (cluster_nc) {
             a.use_wbuf = mode == M_HEUN ? 1 : 0;
+            a.status = h->status_d;
             ND_CUDA(launch_cluster(c.P, prec, a, c.maxD, c.maxDpad, cluster_nc));
         } else if (fused) {
             a.smem = fp64 ? c.smem_fp64 : c.smem_main;

@@ -10,23 +10,25 @@
 // Per field evaluation (Section II.B convolution):
 //   1. forward rows: each CTA transforms its own rows and stores every
 //      spectrum entry straight into the shared memory of the CTA that owns
-//      its column (distributed shared memory stores: no thread waits on a
-//      remote load);
-//   2. cluster barrier;
+//      its column (st.async into distributed shared memory, counted on the
+//      owner's transaction barrier: no thread waits on a remote load or on
+//      its own stores);
+//   2. each CTA waits until its column slots hold every row;
 //   3. columns: one FFT group per (slot, component) transforms its column
 //      from local shared memory, applies the spectral kernel (the x and y
 //      groups of a column exchange their spectra for the in-plane 2x2 block;
 //      the kernel's entries of the CTA's columns are staged in shared memory
 //      once per launch), transforms back and stores the rows into the shared
-//      memory of their owners;
-//   4. cluster barrier;
+//      memory of their owners (st.async again);
+//   4. each CTA waits until its rows hold every column;
 //   5. inverse rows and the per-cell epilogue (stage_update) on the CTA's own
 //      rows; the next stage's forward rows read only those rows, so a CTA
 //      barrier suffices until the next exchange.
 // The state y_n, the stage accumulator and the Heun predictor's normals of the
 // CTA's rows stay in its shared memory for the whole launch: global memory is
-// read once at the start and written once at the end.  The cluster barriers
-// are hardware barriers of co-scheduled CTAs; nothing spins on a flag.
+// read once at the start and written once at the end.  The waits on the
+// transaction barriers give up after about two seconds, set ND_DEV_TIMEOUT in
+// the status word and skip the remaining waits, so a launch always ends.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -67,6 +69,7 @@ __host__ __device__ __forceinline__ size_t cluster_smem_bytes(int D, int Dpad, b
     b += sizeof(T) * (size_t)4 * CG::NTAB * CG::KH;                                     // kernel table
     b += sizeof(T) * (size_t)3 * rpc * Dpad * (wbuf ? 4 : 3);   // stage state, y_n, accumulator (+ normals)
     b += 2 * sizeof(int);                                                               // own cell range
+    b += 16;                                                                            // two mbarriers
     return b;
 }
 
@@ -97,10 +100,65 @@ __device__ __forceinline__ void cluster_packed_scale(cplx<T> *v, const T *s0t, c
     __syncwarp(gmask);
 }
 
+// Distributed-shared-memory exchange with transaction barriers: a producer
+// stores into another CTA's shared memory with st.async, which also counts
+// the bytes on that CTA's mbarrier; the consumer waits until its barrier has
+// seen all the bytes it expects.  No producer waits on its own stores, and
+// each CTA waits only for the data it reads.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_async(uint32_t a, cplx<float> v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 :: "r"(a), "f"(v.x), "f"(v.y), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, cplx<double> v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+                 :: "r"(a), "d"(v.x), "d"(v.y), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase of the given parity to complete, acquiring at
+// cluster scope what the producers stored.  Gives up after about two seconds
+// of the global timer (a producer that never delivers) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    unsigned long long t0 = 0;
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+        if ((it & 63) == 63) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 2000000000ull) return false;
+        }
+    }
+    return false;
+}
+
 template <int P, typename T, int MODE, int NC>
 __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
     k_cluster(const Replica *__restrict__ reps, const int *__restrict__ work, T *__restrict__ ybase,
-              const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base, int use_wbuf)
+              const cplx<T> *__restrict__ twP, long long nsteps, unsigned long long step_base, int use_wbuf,
+              unsigned *__restrict__ status)
 {
     using Gm = FFTGeom<P>;
     using CG = ClusterGeom<P, T, NC>;
@@ -119,7 +177,10 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
     const long long lcs = (long long)rpc * RS;                            // local spectrum component stride
     const long long lms = (long long)rpc * Dpad;                          // local state component stride
     const long long ms_s = (long long)D * Dpad;                           // global state component stride
-    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem);
+    unsigned long long *mbars = reinterpret_cast<unsigned long long *>(smem);   // [0] columns, [1] rows
+    __shared__ int bail_s;                                                      // a wait ran out
+    const uint32_t mb_col = smem_addr(mbars), mb_row = smem_addr(mbars + 1);
+    cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem + 16);
     cplx<T> *colbuf = tw + R1 * G;                                        // [3][P/2][SW]
     cplx<T> *spec = colbuf + 3 * (P / 2) * SW;                            // [3][rpc][RS]
     cplx<T> *scratch = spec + 3 * lcs;
@@ -169,12 +230,30 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
     const bool ctask = gid.group < 3 * SPC;   // groups beyond 3 SPC idle in the column pass
     const int kslot = rank * SPC + cj;
     const bool packed = ctask && kslot == 0;
-    cluster.sync();   // every CTA of the cluster runs (its shared memory exists) before the first remote store
+    if (tid == 0) {
+        mbar_init(mb_col, 1);
+        mbar_init(mb_row, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bail_s = 0;
+    }
+    // bytes each CTA receives from the other CTAs per stage (what it sends to
+    // itself goes by plain stores, made visible by a CTA barrier): its SPC
+    // column slots of every other CTA's rows, and the P/2 + 1 spectrum entries
+    // of each own row from the other CTAs' column slots (rank 0 holds the
+    // packed pair: SPC + 1 entries of its own)
+    const uint32_t bytes_col = (uint32_t)(3 * (D - nloc) * SPC * sizeof(cplx<T>));
+    const uint32_t bytes_row = (uint32_t)(3 * nloc * (P / 2 + 1 - SPC - (rank == 0 ? 1 : 0)) * sizeof(cplx<T>));
+    uint32_t phase = 0;
+    cluster.sync();   // every CTA runs, with its barriers initialised, before the first remote store
     const int c0 = crange[0], c1 = crange[1];
 
     for (long long n = 0; n < nsteps; ++n) {
         const unsigned long long step = step_base + r.step0 + (unsigned long long)n;
         for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
+            if (tid == 0) {
+                mbar_expect(mb_col, bytes_col);
+                mbar_expect(mb_row, bytes_row);
+            }
             // 1. forward rows of the CTA's own rows, sent to the column owners
             for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
@@ -213,22 +292,33 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
                             if (k == 0) {
                                 rA0 = A.x;
                                 rB0 = B.x;
-                            } else if (k == P / 2) {
-                                cplx<T> *dst = cluster.map_shared_rank(colbuf, 0);
-                                dst[(cA * (P / 2) + yA) * SW] = {rA0, A.x};
-                                if (hasB) dst[(cB * (P / 2) + yB) * SW] = {rB0, B.x};
                             } else {
-                                const int ow = k / SPC, j = k - ow * SPC;
-                                cplx<T> *dst = cluster.map_shared_rank(colbuf, ow);
-                                dst[(cA * (P / 2) + yA) * SW + j] = A;
-                                if (hasB) dst[(cB * (P / 2) + yB) * SW + j] = B;
+                                const int ow = k == P / 2 ? 0 : k / SPC, j = k == P / 2 ? 0 : k - ow * SPC;
+                                const cplx<T> a = k == P / 2 ? cplx<T>{rA0, A.x} : A;
+                                const cplx<T> b2 = k == P / 2 ? cplx<T>{rB0, B.x} : B;
+                                const int iA = (cA * (P / 2) + yA) * SW + j, iB = (cB * (P / 2) + yB) * SW + j;
+                                if (ow == rank) {
+                                    colbuf[iA] = a;
+                                    if (hasB) colbuf[iB] = b2;
+                                } else {
+                                    const uint32_t base = cluster_addr(smem_addr(colbuf), ow);
+                                    const uint32_t mb = cluster_addr(mb_col, ow);
+                                    st_async(base + (uint32_t)(iA * sizeof(cplx<T>)), a, mb);
+                                    if (hasB) st_async(base + (uint32_t)(iB * sizeof(cplx<T>)), b2, mb);
+                                }
                             }
                         }
                     }
                 }
                 __syncwarp(gid.gmask);
             }
-            cluster.sync();   // every row spectrum with its column owner
+            // every row spectrum of this CTA's columns has arrived (the
+            // barrier makes the CTA's own plain stores visible)
+            if (!bail_s && !mbar_wait(mb_col, phase & 1)) {
+                bail_s = 1;
+                atomicOr(status, ND_DEV_TIMEOUT);
+            }
+            __syncthreads();
             // 3. columns from the local column buffer, back to the row owners
             {
                 cplx<T> v[R1];
@@ -288,17 +378,34 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
                     const int y = gid.t + G * o;
                     if (ctask && y < D) {
                         const int ow = y / rpc, lr = y - ow * rpc;   // the row's owner
-                        cplx<T> *dst = cluster.map_shared_rank(spec + cc * lcs + (long long)lr * RS, ow);
-                        if (packed) {
-                            dst[0] = {v[o].x, T(0)};
-                            dst[P / 2] = {v[o].y, T(0)};
+                        cplx<T> *dst = spec + cc * lcs + (long long)lr * RS;
+                        if (ow == rank) {
+                            if (packed) {
+                                dst[0] = {v[o].x, T(0)};
+                                dst[P / 2] = {v[o].y, T(0)};
+                            } else {
+                                dst[kx] = v[o];
+                            }
                         } else {
-                            dst[kx] = v[o];
+                            const uint32_t row = cluster_addr(smem_addr(dst), ow);
+                            const uint32_t mb = cluster_addr(mb_row, ow);
+                            if (packed) {
+                                st_async(row, cplx<T>{v[o].x, T(0)}, mb);
+                                st_async(row + (uint32_t)((P / 2) * sizeof(cplx<T>)), cplx<T>{v[o].y, T(0)}, mb);
+                            } else {
+                                st_async(row + (uint32_t)(kx * sizeof(cplx<T>)), v[o], mb);
+                            }
                         }
                     }
                 }
             }
-            cluster.sync();   // every column back with its owner
+            // every column entry of this CTA's rows has arrived
+            if (!bail_s && !mbar_wait(mb_row, phase & 1)) {
+                bail_s = 1;
+                atomicOr(status, ND_DEV_TIMEOUT);
+            }
+            __syncthreads();
+            ++phase;
             // 5. inverse rows of the CTA's own rows (the field rows, in place)
             for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
@@ -379,7 +486,7 @@ static cudaError_t launch_cluster_t(const LaunchArgs &a, int maxD, int maxDpad)
     cudaError_t e = cluster_config<P, T, MODE, NC>(cfg, attr, a.nwork, sm, a.stream);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, k_cluster<P, T, MODE, NC>, a.reps, a.work, (T *)a.y, (const cplx<T> *)a.tw,
-                              a.nsteps, a.step_base, a.use_wbuf);
+                              a.nsteps, a.step_base, a.use_wbuf, a.status);
 }
 
 // Clusters of the size class that can be resident at once (0: the cluster
