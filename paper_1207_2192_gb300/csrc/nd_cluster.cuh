@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
     const long long lms = (long long)rpc * Dpad;                          // local state component stride
     const long long ms_s = (long long)D * Dpad;                           // global state component stride
     unsigned long long *mbars = reinterpret_cast<unsigned long long *>(smem);   // [0] columns, [1] rows
-    __shared__ int bail_s;                                                      // a wait ran out
     const uint32_t mb_col = smem_addr(mbars), mb_row = smem_addr(mbars + 1);
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(smem + 16);
     cplx<T> *colbuf = tw + R1 * G;                                        // [3][P/2][SW]
@@ -234,8 +233,8 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
         mbar_init(mb_col, 1);
         mbar_init(mb_row, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        bail_s = 0;
     }
+    bool bailed = false;   // this thread's wait ran out once: it skips every later wait
     // bytes each CTA receives from the other CTAs per stage (what it sends to
     // itself goes by plain stores, made visible by a CTA barrier): its SPC
     // column slots of every other CTA's rows, and the P/2 + 1 spectrum entries
@@ -314,8 +313,8 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
             }
             // every row spectrum of this CTA's columns has arrived (the
             // barrier makes the CTA's own plain stores visible)
-            if (!bail_s && !mbar_wait(mb_col, phase & 1)) {
-                bail_s = 1;
+            if (!bailed && !mbar_wait(mb_col, phase & 1)) {
+                bailed = true;
                 atomicOr(status, ND_DEV_TIMEOUT);
             }
             __syncthreads();
@@ -400,8 +399,8 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
                 }
             }
             // every column entry of this CTA's rows has arrived
-            if (!bail_s && !mbar_wait(mb_row, phase & 1)) {
-                bail_s = 1;
+            if (!bailed && !mbar_wait(mb_row, phase & 1)) {
+                bailed = true;
                 atomicOr(status, ND_DEV_TIMEOUT);
             }
             __syncthreads();
