@@ -85,3 +85,39 @@ def test_set_damping_per_replica_matches_oracle(O):
         model.set_alpha(a)
         ref = model.heun(g, 4, model.dtau(dt), Ts, 5 + r, 2)
         assert rel(out[r] - g, ref - g, model.mask) < 2e-10, a
+
+
+def test_boundary_rejects_bad_arguments_and_keeps_state():
+    """The error behaviour the header states: bad arguments return
+    ND_ERR_ARG with a message and leave the state untouched; zero steps are a
+    no-op; the handle stays usable afterwards."""
+    import torch
+    with pytest.raises(nd.NDError) as e:
+        nd.nd_create_disk([Disk(-1e-9, 5e-9).desc()])
+    assert e.value.code == nd.ND_ERR_ARG
+    with pytest.raises(nd.NDError):
+        nd.nd_create_disk([])
+    with pytest.raises(nd.NDError):
+        nd.nd_create_disk([Disk(20e-9, 5e-9).desc()], precision=7)
+    disk = Disk(20e-9, 5e-9, alpha=0.02)
+    h = Nanodisk([disk], [2], nd.ND_FP32)
+    m = h.empty_device()
+    h.init_vortex(m, np.zeros((2, 2)))
+    before = m.clone()
+    T, s = np.full(2, 300.0), np.arange(2, dtype=np.uint64)
+    for bad in (lambda: nd.nd_step_rk4(h.h, m, -1, 1e-14),
+                lambda: nd.nd_step_rk4(h.h, m, 1, 0.0),
+                lambda: nd.nd_step_heun(h.h, m, 1, -1e-14, T, s),
+                lambda: nd.nd_step_heun(h.h, m, 1, 1e-14, np.array([300.0, -1.0]), s),
+                lambda: nd.nd_step_heun(h.h, m, -2, 1e-14, T, s)):
+        with pytest.raises(nd.NDError) as e:
+            bad()
+        assert e.value.code == nd.ND_ERR_ARG and nd.nd_last_error()
+    nd.nd_step_rk4(h.h, m, 0, 1e-14)
+    nd.nd_step_heun(h.h, m, 0, 1e-14, T, s)
+    torch.cuda.synchronize()
+    assert torch.equal(m, before)
+    assert nd.nd_check_status(h.h) == nd.ND_OK
+    h.heun(m, 2, 1e-14, T, s)
+    torch.cuda.synchronize()
+    assert not torch.equal(m, before)
