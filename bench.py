@@ -454,17 +454,25 @@ def oracle_rate(workload, budget_s=12.0):
 
 
 def run_reference(args):
-    rates = []
+    """The reference arm: the oracle, as it stands, on the host cores.  Each
+    step is one bounded sample of the workload (its own Heun steps, or for the
+    large disk sampled direct-sum cells); the budget per step keeps the whole
+    run near a minute whatever K and W are."""
+    rates, times = [], []
     sample = ""
     cores = 1
+    budget = min(8.0, max(0.25, 60.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        r, sample, cores = oracle_rate(args.workload, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        t0 = time.perf_counter()
+        r, sample, cores = oracle_rate(args.workload, budget_s=budget)
         if i >= args.warmup:
             rates.append(r)
+            times.append(time.perf_counter() - t0)
     value = statistics.mean(rates)
     return {
         "impl": "reference", "metric": "LLG cell-updates/sec", "value": value, "unit": "cell-updates/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle", "sample": sample},
