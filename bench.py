@@ -364,6 +364,98 @@ def measure(name, steps, warmup, world, local_rank, dist, flush):
     return rec, wl
 
 
+def uneven_record(steps, warmup, world, local_rank, dist, flush):
+    """The uneven batch: 64 disks with R ~ U(20, 100) nm, L/R ~ U(0.05, 0.2)
+    and T ~ U(0, 400) K (ndsynth.uneven_disks, seed 0), the 8 at T = 0 on RK4
+    and the rest on Heun, in two handles tuned together (nd_autotune_group);
+    their 50-step graphs joined into one graph, one launch per bench step,
+    timed the same way as the main workload.  Returns the nested record
+    (rank 0)."""
+    import torch
+    import ndsynth
+    import paper_1207_2192_gb300 as nd
+    R, L, T = ndsynth.uneven_disks(64, seed=0)
+    groups = {"rk4": list(range(8)), "heun": list(range(8, 64))}
+    stream = torch.cuda.current_stream()
+    hs, ms, gs, args_by = {}, {}, {}, {}
+    cells, classes = 0, []
+    built = {}
+    for name, idx in groups.items():
+        built[name] = nd.Nanodisk([nd.Disk(R[i], L[i], alpha=ALPHA) for i in idx], None, nd.ND_FP32)
+    # the plans of both handles tuned together, as their joined graph runs them
+    nd.nd_autotune_group([built["rk4"].h, built["heun"].h], [nd.ND_METHOD_RK4, nd.ND_METHOD_HEUN], DT, CHUNK)
+    for name, idx in groups.items():
+        h = built[name]
+        method = nd.ND_METHOD_RK4 if name == "rk4" else nd.ND_METHOD_HEUN
+        m = h.empty_device()
+        h.init_vortex(m, np.stack([0.1 * R[idx], np.zeros(len(idx))], 1))
+        Tk = T[idx] if name == "heun" else None
+        sd = np.arange(len(idx), dtype=np.uint64) if name == "heun" else None
+        gs[name] = nd.nd_graph_create(h.h, m, method, CHUNK, DT, Tk, sd, step0=0)
+        hs[name], ms[name], args_by[name] = h, m, (method, Tk, sd)
+        cells += sum(h.layout[r]["cells"] for r in range(h.B))
+        c = 0
+        while True:
+            info = nd.nd_plan_info(h.h, c)
+            if info is None:
+                break
+            classes.append({"method": name, "P": info["P"], "replicas": info["replicas"],
+                            "plan": info["plan_rk4" if name == "rk4" else "plan_heun"]})
+            c += 1
+    g = nd.nd_graph_join([gs["rk4"], gs["heun"]])
+    launches_per_step = nd.nd_graph_nodes(g)
+    for _ in range(warmup):
+        nd.nd_graph_launch(g, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        for i in range(steps):
+            l2_flush(torch, flush)
+            ev[i][0].record()
+            nd.nd_graph_launch(g, stream)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
+    value = whole_job_rate(cells * CHUNK * steps, world, total_ms / 1e3)
+    # end to end: both handles stepped through the C ABI on pinned host buffers
+    hosts = {}
+    for name in groups:
+        hosts[name] = torch.empty(hs[name].state_elems, dtype=torch.float32, pin_memory=True)
+        hosts[name].copy_(ms[name].cpu())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_steps = max(3, steps // 4)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        nd.nd_step_rk4(hs["rk4"].h, hosts["rk4"].data_ptr(), CHUNK, DT, None)
+        _, Tk, sd = args_by["heun"]
+        nd.nd_step_heun(hs["heun"].h, hosts["heun"].data_ptr(), CHUNK, DT, Tk, sd, 1000 * CHUNK + i * CHUNK, None)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    nbytes = sum(x.numel() * x.element_size() for x in hosts.values())
+    nd.nd_graph_destroy(g)
+    for x in gs.values():
+        nd.nd_graph_destroy(x)
+    if os.environ.get("RANK", "0") != "0":
+        return None
+    return {
+        "value": value, "unit": "cell-updates/s", "steps": steps, "ms_per_step": total_ms / steps,
+        "config": {"workload": "uneven batch, 64 disks (R 20-100 nm, L/R 0.05-0.2, T 0-400 K; RK4 at T = 0)",
+                   "disks_per_gpu": 64, "cells": cells, "size_classes": classes,
+                   "heun_steps_per_bench_step": CHUNK, "dt_fs": DT * 1e15, "alpha": ALPHA,
+                   "schedule": "two handles' graphs joined into one graph launch (nd_graph_join); classes side by side; "
+                               "plans from nd_autotune_group",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "e2e": {"value": whole_job_rate(cells * CHUNK * e2e_steps, world, e2e_s), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches_per_step * steps, "clocks": clk.summary(),
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -373,10 +465,12 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     rec, wl = measure(args.workload, args.steps, args.warmup, world, local_rank, dist, flush)
-    large = None
+    large = uneven = None
     if args.workload == "batched_heun" and args.large_steps > 0:
         # the HBM-bound configuration, timed the same way, nested in the line
         large, _ = measure("large_disk", args.large_steps, args.warmup, world, local_rank, dist, flush)
+    if args.workload == "batched_heun" and args.uneven_steps > 0:
+        uneven = uneven_record(args.uneven_steps, args.warmup, world, local_rank, dist, flush)
     result = None
     if rank == 0:
         peaks = measured_peaks()
@@ -392,6 +486,8 @@ def run_ours(args, rank, world, local_rank):
             result["hbm_peak_gbs"] = peaks["hbm_gbs"]
         if large is not None:
             result["large_disk"] = large
+        if uneven is not None:
+            result["uneven_batch"] = uneven
     if dist:
         dist.destroy_process_group()
     return result, wl
@@ -491,6 +587,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--large-steps", type=int, default=150,
                     help="bench steps of the nested large-disk record (0: skip it)")
+    ap.add_argument("--uneven-steps", type=int, default=100,
+                    help="bench steps of the nested uneven-batch record (0: skip it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -351,6 +351,16 @@ int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_
  * threads per CTA; cluster: threads of the cluster; 0: global path).  Returns
  * ND_ERR_ARG for cls out of range.  The paper has no counterpart. */
 int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream);
+
+/* Autotuning of handles that will step side by side (for instance the RK4
+ * and Heun handles of one batch whose graphs nd_graph_join replays as one):
+ * like nd_autotune, but every candidate of every class of every handle is
+ * timed on all n handles stepping together, each on its own stream, with the
+ * other classes at their current plans, so that the plans share the GPU well
+ * rather than each being fastest alone.  methods[k] is handle k's method.
+ * ND_ERR_ARG for no handles, a repeated handle or a bad method. */
+int nd_autotune_group(nd_handle *const *handles, const int *methods, int n, double dt_seconds, long long n_steps,
+                      void *stream);
 /* Force the plan of class cls for a method (-1 default, 0..2 fused variant,
  * 100 global path, 200 cluster of 8 CTAs, 201 cluster of 16 CTAs); ND_ERR_ARG
  * if it does not exist or does not fit.  Plans 0..2 and 100 compute the same arithmetic per element, so

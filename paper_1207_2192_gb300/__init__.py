@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _binding as _b
-from ._binding import (ND_METHOD_HEUN, ND_METHOD_RK4, nd_autotune, nd_plan_info, nd_set_plan, nd_graph_create, nd_graph_destroy, nd_graph_launch,
+from ._binding import (ND_METHOD_HEUN, ND_METHOD_RK4, nd_autotune, nd_autotune_group, nd_plan_info, nd_set_plan, nd_graph_create, nd_graph_destroy, nd_graph_launch,
                        nd_graph_join,
                        nd_graph_nodes, nd_check_status, nd_selftest_handover_timeout, nd_series_reset,
                        nd_series_sample, nd_series_read, nd_power_spectrum, ND_GRAPH_STATS, ND_GRAPH_SERIES, ND_ERR_ARG, ND_ERR_CUDA, ND_ERR_NAN, ND_ERR_NO_VORTEX, ND_ERR_NOT_CONVERGED, ND_ERR_TIMEOUT,
@@ -30,7 +30,7 @@ __all__ = ["Disk", "Nanodisk", "NDError", "ND_FP32", "ND_FP64", "ND_GRID_3X", "n
            "nd_stats_reset", "nd_stats_sample", "nd_stats_read", "nd_stats_save", "nd_stats_load", "nd_check_status", "nd_selftest_handover_timeout",
            "nd_series_reset", "nd_series_sample", "nd_series_read", "nd_power_spectrum", "ND_GRAPH_STATS", "ND_GRAPH_SERIES",
            "nd_graph_create", "nd_graph_launch", "nd_graph_join", "nd_graph_nodes", "nd_graph_destroy",
-           "nd_autotune", "nd_plan_info", "nd_set_plan"]
+           "nd_autotune", "nd_autotune_group", "nd_plan_info", "nd_set_plan"]
 
 
 @dataclass

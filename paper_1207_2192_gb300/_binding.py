@@ -69,6 +69,7 @@ SIGNATURES = {
     "nd_selftest_handover_timeout": (_I, [_P, _P]),
     "nd_graph_create": (_I, [_P, _P, _I, _LL, _D, _P, _P, _ULL, _I, _P]),
     "nd_autotune": (_I, [_P, _I, _D, _LL, _P]),
+    "nd_autotune_group": (_I, [_P, _P, _I, _D, _LL, _P]),
     "nd_set_plan": (_I, [_P, _I, _I, _I]),
     "nd_plan_info": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "nd_graph_launch": (_I, [_P, _P]),
@@ -390,6 +391,14 @@ def nd_graph_nodes(g):
 
 def nd_graph_destroy(g):
     lib().nd_graph_destroy(g)
+
+
+def nd_autotune_group(handles, methods, dt_seconds, n_steps=20, stream=None):
+    """Tune the plans of several handles timed stepping side by side."""
+    hs = (ctypes.c_void_p * len(handles))(*handles)
+    ms = (ctypes.c_int * len(methods))(*methods)
+    _check(lib().nd_autotune_group(ctypes.cast(hs, _P), ctypes.cast(ms, _P), len(handles), dt_seconds, n_steps,
+                                   _stream(stream)))
 
 
 def nd_autotune(h, method, dt_seconds, n_steps=20, stream=None):

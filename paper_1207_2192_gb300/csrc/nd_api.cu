@@ -1393,74 +1393,178 @@ int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_
     return ND_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------- autotuning
+
+// The plans a size class can step with in a mode: the one-CTA kernel's thread
+// counts that fit, the global path, and the cluster plans the GPU can hold.
+static std::vector<int> plan_candidates(const nd_handle *h, const SizeClass &c, int mode)
+{
+    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
+    std::vector<int> cands;
+    for (int v = 0; v < 3; ++v) {
+        if (fused_variant_threads(c.P, v) == 0) continue;
+        const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, v);
+        if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(v);
+    }
+    cands.push_back(kPlanGlobal);
+    for (int pl : {kPlanCluster, kPlanCluster16})
+        if (cluster_plan_fits(h, c, prec, mode == M_HEUN, plan_cluster_nc(pl))) cands.push_back(pl);
+    return cands;
+}
+
+namespace {
+// One handle being tuned: its method, a scratch state and its own stream.
+struct TuneItem {
+    nd_handle *h = nullptr;
+    int mode = M_HEUN, slot = 1;
+    void *tmp = nullptr;
+    std::vector<double> T;
+    std::vector<unsigned long long> sd;
+    cudaStream_t st = nullptr;
+};
+}  // namespace
+
+// The steps of every item side by side (each handle on its stream, forked
+// from and joined back to st0); only_class >= 0 restricts a single item to
+// that class.
+static int tune_run(std::vector<TuneItem> &items, double dt, long long n_steps, cudaStream_t st0, cudaEvent_t fork,
+                    const std::vector<cudaEvent_t> &joins, int only_class)
+{
+    const bool many = items.size() > 1;
+    if (many) ND_CUDA(cudaEventRecord(fork, st0));
+    for (size_t k = 0; k < items.size(); ++k) {
+        TuneItem &it = items[k];
+        const cudaStream_t s = many ? it.st : st0;
+        if (many) ND_CUDA(cudaStreamWaitEvent(s, fork, 0));
+        const bool heun = it.mode == M_HEUN;
+        fill_reps(it.h, it.h->prec == ND_FP64, dt, heun ? it.T.data() : nullptr, heun ? it.sd.data() : nullptr, 0);
+        upload_reps(it.h, s);
+        if (int rc = run_mode(it.h, it.mode, false, it.tmp, nullptr, n_steps, s, nullptr, only_class)) return rc;
+        if (many) {
+            ND_CUDA(cudaEventRecord(joins[k], s));
+            ND_CUDA(cudaStreamWaitEvent(st0, joins[k], 0));
+        }
+    }
+    return ND_OK;
+}
+
+// One pass of coordinate descent over every class of every item: each
+// candidate plan is timed (one warm-up, the fastest of three runs) on
+// everything that shares the GPU -- the whole group of handles, or the whole
+// handle when it has several classes, which step side by side -- with the
+// other classes at their current plans.  A plan that is fastest alone (a
+// cluster plan spreading few replicas over many SMs) can take SMs that the
+// other classes need, so a class is never timed alone unless it is alone.
+static int tune_items(std::vector<TuneItem> &items, double dt, long long n_steps, cudaStream_t st0)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr, fork = nullptr;
+    std::vector<cudaEvent_t> joins(items.size(), nullptr);
+    int rc = ND_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(ND_ERR_CUDA, "autotune events");
+    for (auto &j : joins)
+        if (rc == ND_OK && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(ND_ERR_CUDA, "autotune events");
+    const bool whole = items.size() > 1 || items[0].h->classes.size() > 1;
+    for (auto &it : items) {
+        for (int ci = 0; ci < (int)it.h->classes.size() && rc == ND_OK; ++ci) {
+            SizeClass &c = it.h->classes[ci];
+            const std::vector<int> cands = plan_candidates(it.h, c, it.mode);
+            float best_ms = 1e30f;
+            int best = cands.front();
+            for (int cand : cands) {
+                c.plan[it.slot] = cand;
+                const int only = whole ? -1 : ci;
+                rc = tune_run(items, dt, n_steps, st0, fork, joins, only);   // warm-up, builds schedules
+                if (rc) break;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3 && rc == ND_OK; ++rep) {
+                    cudaEventRecord(e0, st0);
+                    rc = tune_run(items, dt, n_steps, st0, fork, joins, only);
+                    cudaEventRecord(e1, st0);
+                    if (rc) break;
+                    cudaEventSynchronize(e1);
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = std::min(ms, t);
+                }
+                if (rc) break;
+                if (ms < best_ms) { best_ms = ms; best = cand; }
+            }
+            c.plan[it.slot] = best;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (fork) cudaEventDestroy(fork);
+    for (auto j : joins)
+        if (j) cudaEventDestroy(j);
+    return rc;
+}
+
+// A tuning item for handle h: global-path buffers (a candidate), a scratch
+// state holding the analytic centred vortex, 300 K and seeds 0..B-1.
+static int tune_item_make(nd_handle *h, int method, cudaStream_t st, TuneItem &it)
+{
+    if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
+    if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
+    const int B = (int)h->rep_disk.size();
+    it.h = h;
+    it.mode = method == ND_METHOD_RK4 ? M_RK4 : M_HEUN;
+    it.slot = method == ND_METHOD_RK4 ? 0 : 1;
+    ND_CUDA(cudaMalloc(&it.tmp, h->elt * h->state_elems));
+    std::vector<double> X0(2 * B, 0.0);
+    if (int rc = nd_init_vortex(h, it.tmp, X0.data(), st)) return rc;
+    it.T.assign(B, 300.0);
+    it.sd.resize(B);
+    for (int r = 0; r < B; ++r) it.sd[r] = (unsigned long long)r;
+    return ND_OK;
+}
+
+extern "C" {
+
 int nd_autotune(nd_handle *h, int method, double dt_seconds, long long n_steps, void *stream)
 {
     if (int rc = check_handle(h)) return rc;
     if (method != ND_METHOD_RK4 && method != ND_METHOD_HEUN) return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
     if (n_steps < 1 || !(dt_seconds > 0)) return fail(ND_ERR_ARG, "n_steps >= 1 and dt > 0 required");
     cudaStream_t st = (cudaStream_t)stream;
-    const int mode = method == ND_METHOD_RK4 ? M_RK4 : M_HEUN, slot = method == ND_METHOD_RK4 ? 0 : 1;
-    const int B = (int)h->rep_disk.size();
-    const int prec = h->prec == ND_FP64 ? ND_PREC_FP64 : ND_PREC_FP32;
-    // candidates may include the global path: make sure its buffers exist
-    if (int rc = ensure_alloc(&h->ms, h->elt * h->state_elems)) return rc;
-    if (int rc = ensure_alloc(&h->spec, sizeof(double) * 2 * h->spec_words)) return rc;
-    void *tmp = nullptr;
-    ND_CUDA(cudaMalloc(&tmp, h->elt * h->state_elems));
-    std::vector<double> X0(2 * B, 0.0);
-    int rc = nd_init_vortex(h, tmp, X0.data(), stream);
-    std::vector<double> T(B, 300.0);
-    std::vector<unsigned long long> sd(B);
-    for (int r = 0; r < B; ++r) sd[r] = (unsigned long long)r;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    // With several size classes the classes step side by side and share the
-    // GPU, so each candidate is timed on the whole handle with the other
-    // classes at their current plans (one pass of coordinate descent), not on
-    // its class alone: a plan that is fastest alone (a cluster plan spreading
-    // few replicas over many SMs) can take SMs the other classes need.
-    const int only = h->classes.size() > 1 ? -1 : 0;
-    for (int ci = 0; ci < (int)h->classes.size() && rc == ND_OK; ++ci) {
-        SizeClass &c = h->classes[ci];
-        std::vector<int> cands;
-        for (int v = 0; v < 3; ++v) {
-            if (fused_variant_threads(c.P, v) == 0) continue;
-            const size_t sm = fused_smem(c.P, prec, c.maxD, c.maxDpad, false, v);
-            if (sm != (size_t)-1 && sm + 1024 <= h->max_smem) cands.push_back(v);
-        }
-        cands.push_back(kPlanGlobal);
-        for (int pl : {kPlanCluster, kPlanCluster16})
-            if (cluster_plan_fits(h, c, prec, mode == M_HEUN, plan_cluster_nc(pl))) cands.push_back(pl);
-        float best_ms = 1e30f;
-        int best = cands.front();
-        for (int cand : cands) {
-            c.plan[slot] = cand;
-            fill_reps(h, h->prec == ND_FP64, dt_seconds, mode == M_HEUN ? T.data() : nullptr, mode == M_HEUN ? sd.data() : nullptr, 0);
-            upload_reps(h, st);
-            const int which = only < 0 ? -1 : ci;
-            rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, which);   // warm-up, builds schedules
-            if (rc) break;
-            // the fastest of three timed runs: one run is at the mercy of clock ramps and neighbours
-            float ms = 1e30f;
-            for (int rep = 0; rep < 3 && rc == ND_OK; ++rep) {
-                cudaEventRecord(e0, st);
-                rc = run_mode(h, mode, false, tmp, nullptr, n_steps, st, nullptr, which);
-                cudaEventRecord(e1, st);
-                if (rc) break;
-                cudaEventSynchronize(e1);
-                float t = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                ms = std::min(ms, t);
-            }
-            if (rc) break;
-            if (ms < best_ms) { best_ms = ms; best = cand; }
-        }
-        c.plan[slot] = best;
+    std::vector<TuneItem> items(1);
+    int rc = tune_item_make(h, method, st, items[0]);
+    if (rc == ND_OK) rc = tune_items(items, dt_seconds, n_steps, st);
+    cudaFree(items[0].tmp);
+    return rc;
+}
+
+int nd_autotune_group(nd_handle *const *hs, const int *methods, int n, double dt_seconds, long long n_steps,
+                      void *stream)
+{
+    if (!hs || !methods || n < 1) return fail(ND_ERR_ARG, "no handles to tune");
+    if (n_steps < 1 || !(dt_seconds > 0)) return fail(ND_ERR_ARG, "n_steps >= 1 and dt > 0 required");
+    for (int k = 0; k < n; ++k) {
+        if (int rc = check_handle(hs[k])) return rc;
+        if (methods[k] != ND_METHOD_RK4 && methods[k] != ND_METHOD_HEUN)
+            return fail(ND_ERR_ARG, "method must be RK4 or HEUN");
+        for (int j = 0; j < k; ++j)
+            if (hs[j] == hs[k]) return fail(ND_ERR_ARG, "a handle appears twice in the group");
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(tmp);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<TuneItem> items(n);
+    int rc = ND_OK;
+    for (int k = 0; k < n && rc == ND_OK; ++k) {
+        rc = tune_item_make(hs[k], methods[k], st, items[k]);
+        if (rc == ND_OK && n > 1 && cudaStreamCreateWithFlags(&items[k].st, cudaStreamNonBlocking) != cudaSuccess)
+            rc = fail(ND_ERR_CUDA, "autotune streams");
+    }
+    if (rc == ND_OK) rc = tune_items(items, dt_seconds, n_steps, st);
+    cudaStreamSynchronize(st);
+    for (auto &it : items) {
+        if (it.st) cudaStreamDestroy(it.st);
+        cudaFree(it.tmp);
+    }
     return rc;
 }
 

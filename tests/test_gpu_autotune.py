@@ -67,3 +67,25 @@ def test_autotune_picks_valid_plans():
     h.init_vortex(m, np.zeros((h.B, 2)))
     h.heun(m, 2, 1e-14, np.full(h.B, 300.0), np.arange(h.B, dtype=np.uint64))
     assert nd.nd_check_status(h.h) == nd.ND_OK
+
+
+def test_group_autotune_keeps_valid_plans_for_handles_that_share_the_gpu():
+    """nd_autotune_group times the classes of several handles stepping side by
+    side; every class ends on a valid plan and the handles still step."""
+    ha = Nanodisk([Disk(13e-9, 3e-9), Disk(50e-9, 10e-9)], [1, 2], nd.ND_FP32)
+    hb = Nanodisk([Disk(24e-9, 5e-9, alpha=0.02), Disk(70e-9, 10e-9, alpha=0.02)], [3, 2], nd.ND_FP32)
+    nd.nd_autotune_group([ha.h, hb.h], [nd.ND_METHOD_RK4, nd.ND_METHOD_HEUN], 1e-14, 4)
+    for h, key in ((ha, "plan_rk4"), (hb, "plan_heun")):
+        for c in classes(h):
+            assert c[key] in (0, 1, 2, 100, 200, 201)
+    ma, mb = ha.empty_device(), hb.empty_device()
+    ha.init_vortex(ma, np.zeros((ha.B, 2)))
+    hb.init_vortex(mb, np.zeros((hb.B, 2)))
+    ha.rk4(ma, 2, 1e-14)
+    hb.heun(mb, 2, 1e-14, np.full(hb.B, 300.0), np.arange(hb.B, dtype=np.uint64))
+    torch.cuda.synchronize()
+    assert nd.nd_check_status(ha.h) == nd.ND_OK and nd.nd_check_status(hb.h) == nd.ND_OK
+    with pytest.raises(nd.NDError):
+        nd.nd_autotune_group([ha.h, ha.h], [nd.ND_METHOD_RK4, nd.ND_METHOD_RK4], 1e-14, 2)
+    with pytest.raises(nd.NDError):
+        nd.nd_autotune_group([], [], 1e-14, 2)
