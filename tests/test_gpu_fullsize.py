@@ -10,6 +10,7 @@ configuration the benchmark times.
   SMs): sampled replicas against the oracle's Heun trajectory.
 """
 import numpy as np
+import torch
 import pytest
 
 import ndsynth
@@ -79,26 +80,34 @@ def test_large_disk_heun_properties():
 def test_uneven_batch_full_size_with_graphs_and_autotuned_plans(O):
     """The uneven batch: 64 disks with R ~ U(20, 100) nm, L/R ~ U(0.05, 0.2)
     and T ~ U(0, 400) K, disks 0-7 at T = 0 stepping with RK4 and the rest
-    with Heun, size classes P = 64, 128 and 256 (on-chip and global paths).
-    Each method's handle is autotuned and its steps captured in one CUDA
-    graph; sampled disks of every size class match their oracle trajectory."""
+    with Heun, size classes P = 64, 128 and 256 (on-chip, cluster and global
+    paths), in the launch configuration the bench times: both handles tuned
+    together (nd_autotune_group), each handle's steps captured in a CUDA
+    graph and the two graphs joined into one launch.  Sampled disks of every
+    size class match their oracle trajectory."""
     R, L, T = ndsynth.uneven_disks(64, seed=0)
     alpha, dt, steps = 0.01, 1e-14, 2
     groups = {"rk4": list(range(8)), "heun": list(range(8, 64))}
-    hs, ms, starts = {}, {}, {}
+    hs, ms, starts, gs = {}, {}, {}, {}
     for name, idx in groups.items():
-        h = Nanodisk([Disk(R[i], L[i], alpha=alpha) for i in idx], None, nd.ND_FP32)
+        hs[name] = Nanodisk([Disk(R[i], L[i], alpha=alpha) for i in idx], None, nd.ND_FP32)
+    nd.nd_autotune_group([hs["rk4"].h, hs["heun"].h], [nd.ND_METHOD_RK4, nd.ND_METHOD_HEUN], dt, 4)
+    for name, idx in groups.items():
+        h = hs[name]
         method = nd.ND_METHOD_RK4 if name == "rk4" else nd.ND_METHOD_HEUN
-        nd.nd_autotune(h.h, method, dt, n_steps=4)
         m = h.empty_device()
         h.init_vortex(m, np.stack([0.1 * R[idx], np.zeros(len(idx))], 1))
         starts[name] = h.unpack(m)
         Tk = T[idx] if name == "heun" else None
         seeds = np.arange(len(idx), dtype=np.uint64) + 100 if name == "heun" else None
-        g = nd.nd_graph_create(h.h, m, method, steps, dt, Tk, seeds, step0=0)
-        nd.nd_graph_launch(g)
+        gs[name] = nd.nd_graph_create(h.h, m, method, steps, dt, Tk, seeds, step0=0)
+        ms[name] = m
+    joined = nd.nd_graph_join([gs["rk4"], gs["heun"]])
+    nd.nd_graph_launch(joined)
+    torch.cuda.synchronize()
+    nd.nd_graph_destroy(joined)
+    for g in gs.values():
         nd.nd_graph_destroy(g)
-        hs[name], ms[name] = h, m
     Ps = {name: sorted({hs[name].layout[r]["P"] for r in range(hs[name].B)}) for name in groups}
     assert Ps["heun"][0] <= 64 and Ps["heun"][-1] == 256
     for name, idx in groups.items():
