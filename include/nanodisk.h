@@ -337,13 +337,14 @@ int nd_power_spectrum(nd_handle *h, int component, int window, double dt_sample_
  * on-chip kernel with one of up to three thread counts (which set how many
  * FFT groups share the row and column passes), on the global-memory path, or
  * (P <= 128) with each replica spread over a thread-block cluster of 8 CTAs
- * (or 16 for P >= 32; P = 256 on 16) whose shared memories hold the
+ * (or 16 for P >= 32; P = 192 and 256 on 16) whose shared memories hold the
  * replica's rows and exchange columns through distributed shared memory (for
  * classes with too few replicas to fill the GPU with one CTA each).
  * nd_autotune times every candidate that fits, on a scratch copy of an
  * analytic vortex state, for n_steps steps of the given method (and, for
  * Heun, 300 K; the fastest of three runs), and keeps the fastest per class
- * for later nd_step_* calls and graphs.  In a handle of several classes,
+ * for later nd_step_* calls and graphs (the class's current plan unless
+ * another is faster by more than 2%).  In a handle of several classes,
  * which step side by side, each candidate is timed on the whole handle with
  * the other classes at their current plans (one pass over the classes).  nd_plan_info reports, for class cls (0-based, in order of first
  * appearance), its P, replica count, the chosen plans (-1 default, 0..2 fused

@@ -1472,7 +1472,14 @@ static int tune_items(std::vector<TuneItem> &items, double dt, long long n_steps
     for (auto &it : items) {
         for (int ci = 0; ci < (int)it.h->classes.size() && rc == ND_OK; ++ci) {
             SizeClass &c = it.h->classes[ci];
-            const std::vector<int> cands = plan_candidates(it.h, c, it.mode);
+            // the class's current plan is timed first and kept unless another
+            // is faster by more than 2%, so that timing noise does not walk the
+            // descent between near-equal plans
+            std::vector<int> cands = plan_candidates(it.h, c, it.mode);
+            int cur = c.plan[it.slot];
+            if (cur == -1) cur = c.fused_main ? 0 : kPlanGlobal;   // what the default runs
+            const auto pos = std::find(cands.begin(), cands.end(), cur);
+            if (pos != cands.end()) std::rotate(cands.begin(), pos, pos + 1);
             float best_ms = 1e30f;
             int best = cands.front();
             for (int cand : cands) {
@@ -1492,7 +1499,7 @@ static int tune_items(std::vector<TuneItem> &items, double dt, long long n_steps
                     ms = std::min(ms, t);
                 }
                 if (rc) break;
-                if (ms < best_ms) { best_ms = ms; best = cand; }
+                if (ms < (cand == cands.front() ? 1.0f : 0.98f) * best_ms) { best_ms = ms; best = cand; }
             }
             c.plan[it.slot] = best;
         }

@@ -55,9 +55,10 @@ cudaError_t launch_fused_f32(int P, const LaunchArgs &a)
 }
 
 // Cluster plans: NC = 8 CTAs for every on-chip size, NC = 16 for P >= 32
-// (where the P/2 column slots split over 16 CTAs), and P = 256 on 16 CTAs.
+// (where the P/2 column slots split over 16 CTAs), and P = 192 and 256 on 16
+// CTAs (spectra too large for one CTA's shared memory).
 #define ND_CLUSTER_CASES(X)      \
-    X(16, 8) X(32, 8) X(64, 8) X(128, 8) X(32, 16) X(64, 16) X(128, 16) X(256, 16)
+    X(16, 8) X(32, 8) X(64, 8) X(128, 8) X(32, 16) X(64, 16) X(128, 16) X(192, 16) X(256, 16)
 
 size_t cluster_smem_f32(int P, int D, int Dpad, bool wbuf, int nc)
 {

@@ -133,18 +133,20 @@ def test_cluster_plan_is_offered_by_autotune():
     assert nd.nd_plan_info(h.h, 0)["plan_heun"] in (0, 1, 2, 100, 200, 201)
 
 
+@pytest.mark.parametrize("R,grid3x,P", [(70e-9, False, 256), (80e-9, True, 192)])
 @pytest.mark.parametrize("method", [nd.ND_METHOD_HEUN, nd.ND_METHOD_RK4])
-def test_p256_cluster_plan_matches_global_path_and_oracle(O, method):
-    """P = 256 (D = 70): the spectrum of one replica is too large for one
-    CTA's shared memory but fits in a 16-CTA cluster's; against the global
-    path (plan 100) and the oracle."""
-    disk = Disk(70e-9, 10e-9, alpha=0.02, hext=(1e3, 0.0, -2e3))
-    h = Nanodisk([disk], [2], nd.ND_FP32)
-    assert h.layout[0]["P"] == 256
+def test_large_grid_cluster_plan_matches_global_path_and_oracle(O, method, R, grid3x, P):
+    """P = 256 (D = 70) and P = 192 (D = 80, the radix-3 grid): the spectrum
+    of one replica is too large for one CTA's shared memory but fits in a
+    16-CTA cluster's; against the global path (plan 100) and the oracle."""
+    disk = Disk(R, 10e-9, alpha=0.02, hext=(1e3, 0.0, -2e3))
+    h = Nanodisk([disk], [2], nd.ND_FP32, grid3x=grid3x)
+    assert h.layout[0]["P"] == P
     assert nd.nd_set_plan(h.h, 0, method, 200, check=False) == nd.ND_ERR_ARG      # 8 CTAs: no such plan
     nd.nd_set_plan(h.h, 0, method, 201)
-    assert nd.nd_plan_info(h.h, 0)["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] == 16 * 512
-    hg = Nanodisk([disk], [2], nd.ND_FP32)
+    nt = 512 if P >= 256 else 256
+    assert nd.nd_plan_info(h.h, 0)["threads_heun" if method == nd.ND_METHOD_HEUN else "threads_rk4"] == 16 * nt
+    hg = Nanodisk([disk], [2], nd.ND_FP32, grid3x=grid3x)
     nd.nd_set_plan(hg.h, 0, method, 100)
     X0 = np.array([[3e-9, 1e-9], [-2e-9, 0.0]])
     out, ref = run(h, method, 3, X0), run(hg, method, 3, X0)
