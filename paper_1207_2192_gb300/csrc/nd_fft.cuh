@@ -214,7 +214,9 @@ enum : int { FFT_FULL = 0, FFT_HALF_IN = 1, FFT_HALF_OUT = 2 };
 //   FL     : FFT_HALF_IN when elements >= P/2 are zero (registers o >= R1/2
 //            are then not read), FFT_HALF_OUT when only elements < P/2 of the
 //            result are needed (registers o >= R1/2 are then undefined)
-template <int P, int DIR, int FL = FFT_FULL, typename T>
+//   TWS    : row stride of the twiddle table (G by default; 2G reads the
+//            table of a 2P-point transform, whose even rows are this one's)
+template <int P, int DIR, int FL = FFT_FULL, int TWS = FFTGeom<P>::G, typename T>
 __device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const cplx<T> *tw, unsigned gmask)
 {
     using Gm = FFTGeom<P>;
@@ -223,7 +225,7 @@ __device__ __forceinline__ void fft_group(cplx<T> *v, int t, cplx<T> *scr, const
     else dft_reg<R1, DIR>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) {
-        cplx<T> w = tw[k1 * G + t];
+        cplx<T> w = tw[k1 * TWS + t];
         v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
     }
 #pragma unroll

@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
         }
         __syncthreads();
 
-        const int nrow = row_tasks(D);
+        // row tasks: one real row each (half-length transforms) at P = 128,
+        // else a complex row pair each
+        constexpr bool HR = HalfRows<P>::on;
+        const int nrow = HR ? 3 * D : row_tasks(D);
         double esum = 0.0;
         T relX = 0, relY = 0;
         if (MODE == M_RELAX) {
@@ -364,7 +367,16 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
             for (int stage = 0; stage < ModeStages<MODE>::n; ++stage) {
                 for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
                     const int q = qb + gw;
-                    row_fwd_task<P, T>(q, q < nrow, D, msm, Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw, gid.gmask);
+                    if constexpr (HR) {
+                        const int c = q / D, y = q - c * D;
+                        const bool act = q < nrow;
+                        const int cc = act ? c : 0, yy = act ? y : 0;
+                        row_fwd_half<P, T>(act, msm + cc * ms_s + (long long)yy * Dpad, D,
+                                           spec + cc * cs + (long long)yy * RS, gid.t, scr, tw, gid.gmask);
+                    } else {
+                        row_fwd_task<P, T>(q, q < nrow, D, msm, Dpad, ms_s, spec, cs, gid.t, gid.lane, scr, tw,
+                                           gid.gmask);
+                    }
                 }
                 __syncthreads();
                 for (int qb = warp * GPW; qb < ncol; qb += NW * GPW) {
@@ -375,7 +387,15 @@ __global__ void __launch_bounds__(NT, (FusedMinBlocks<P, NT>::v))
                 __syncthreads();
                 for (int qb = warp * GPW; qb < nrow; qb += NW * GPW) {
                     const int q = qb + gw;
-                    row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+                    if constexpr (HR) {
+                        const int c = q / D, y = q - c * D;
+                        const bool act = q < nrow;
+                        const int cc = act ? c : 0, yy = act ? y : 0;
+                        cplx<T> *row = spec + cc * cs + (long long)yy * RS;
+                        row_inv_half<P, T>(act, row, D, reinterpret_cast<T *>(row), gid.t, scr, tw, gid.gmask);
+                    } else {
+                        row_inv_task<P, T>(q, q < nrow, D, spec, cs, gid.t, scr, tw, gid.gmask);
+                    }
                 }
                 __syncthreads();
                 const T *hr = reinterpret_cast<const T *>(spec);

@@ -451,6 +451,96 @@ __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> 
     }
 }
 
+// ------------------------------------------------- half-length real rows
+
+// One real row per task, as a transform of half the length (for P = 128,
+// where the P/2-point transform runs on groups of the same width): 3D tasks
+// of half the work each instead of D + D/2 paired ones, so that the row
+// passes divide over the CTA's groups in finer steps.  With M = P/2 and
+// W = exp(-2 pi i / P):
+//   forward: z[n] = x[2n] + i x[2n+1] (n < M), Z = FFT_M(z),
+//            X[k] = (Z[k] + conj Z[M-k])/2 - i W^k (Z[k] - conj Z[M-k])/2,
+//            k = 0..M (X[M] = Re Z[0] - Im Z[0]);
+//   inverse: Z[k] = (X[k] + conj X[M-k]) + i W^-k (X[k] - conj X[M-k]),
+//            z = IFFT_M(Z), x[2n] = Re z[n], x[2n+1] = Im z[n]
+// (both unnormalised, as the paired transforms).  twP is the P-point table
+// [R1][G] of the groups' own transforms: its even rows are the M-point one's,
+// and its row 1 holds W^t.
+template <int P> struct HalfRows { static constexpr bool on = false; };
+template <> struct HalfRows<128> { static constexpr bool on = FFTGeom<64>::G == FFTGeom<128>::G; };
+
+// Forward: the real row x (x[i], i < D; zero beyond) to its half spectrum
+// X[0..M] in dst.
+template <int P, typename T>
+__device__ __forceinline__ void row_fwd_half(bool active, const T *x, int D, cplx<T> *dst, int t, cplx<T> *scr,
+                                             const cplx<T> *twP, unsigned gmask)
+{
+    constexpr int M = P / 2, G = FFTGeom<M>::G, R1 = FFTGeom<M>::R1;
+    cplx<T> v[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
+#pragma unroll
+    for (int o = 0; o < R1 / 2; ++o) {   // D <= M: the upper half of z is zero padding
+        const int n = t + G * o;
+        if (active) {
+            const T a = 2 * n < D ? x[2 * n] : T(0), b = 2 * n + 1 < D ? x[2 * n + 1] : T(0);
+            v[o] = {a, b};
+        }
+    }
+    fft_group<M, -1, FFT_HALF_IN, 2 * G>(v, t, scr, twP, gmask);
+    mirror_put<M>(v, scr, t);
+    __syncwarp(gmask);
+    if (active) {
+        const cplx<T> w1 = twP[G + t];   // W^t
+        const T h = T(0.5);
+#pragma unroll
+        for (int o = 0; o < R1; ++o) {
+            const int k = t + G * o;
+            const cplx<T> z = v[o], zm = mirror_get<M>(scr, k);
+            const cplx<T> e = {h * (z.x + zm.x), h * (z.y - zm.y)};   // (Z[k] + conj Z[M-k]) / 2
+            const cplx<T> d = {h * (z.x - zm.x), h * (z.y + zm.y)};   // (Z[k] - conj Z[M-k]) / 2
+            const cplx<T> wd = cmul(twid<-1>(w1, o, P / G), d);        // W^k d, W^k = W^t W^(G o)
+            dst[k] = {e.x + wd.y, e.y - wd.x};                          // e - i W^k d
+        }
+        if (t == 0) dst[M] = {v[0].x - v[0].y, T(0)};
+    }
+    __syncwarp(gmask);
+}
+
+// Inverse: the half spectrum X[0..M] in src to the real row, x[i] for i < D
+// written to out (which may alias src: every read precedes the writes).
+template <int P, typename T>
+__device__ __forceinline__ void row_inv_half(bool active, const cplx<T> *src, int D, T *out, int t, cplx<T> *scr,
+                                             const cplx<T> *twP, unsigned gmask)
+{
+    constexpr int M = P / 2, G = FFTGeom<M>::G, R1 = FFTGeom<M>::R1;
+    cplx<T> v[R1];
+    const cplx<T> w1 = twP[G + t];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        const int k = t + G * o;
+        cplx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
+        if (active) {
+            a = src[k];
+            b = src[M - k];
+        }
+        const cplx<T> s = {a.x + b.x, a.y - b.y};                     // X[k] + conj X[M-k]
+        const cplx<T> d = {a.x - b.x, a.y + b.y};                     // X[k] - conj X[M-k]
+        const cplx<T> wk = twid<-1>(w1, o, P / G);                    // W^k
+        const cplx<T> wd = {wk.x * d.x + wk.y * d.y, wk.x * d.y - wk.y * d.x};   // W^-k d
+        v[o] = {s.x - wd.y, s.y + wd.x};                                // s + i W^-k d
+    }
+    fft_group<M, +1, FFT_HALF_OUT, 2 * G>(v, t, scr, twP, gmask);
+    if (active) {
+#pragma unroll
+        for (int o = 0; o < R1 / 2; ++o) {
+            const int n = t + G * o;
+            if (2 * n < D) out[2 * n] = v[o].x;
+            if (2 * n + 1 < D) out[2 * n + 1] = v[o].y;
+        }
+    }
+}
+
 // --------------------------------------------------------- group plumbing
 
 template <int P> struct GroupId {

@@ -1,6 +1,7 @@
 """The stepping plans (fused-kernel thread-count variants, global path) give
-bit-identical trajectories, and the autotuner picks one of the valid plans
-per size class."""
+bit-identical trajectories (to rounding where the global path transforms the
+rows differently), and the autotuner picks one of the valid plans per size
+class."""
 import numpy as np
 import pytest
 import torch
@@ -52,7 +53,13 @@ def test_every_plan_gives_the_same_trajectory(method):
             if nd.nd_set_plan(h.h, ci, method, plan, check=False) != nd.ND_OK:
                 continue
             tried += 1
-            assert torch.equal(run(h), ref), (ci, plan)
+            out = run(h)
+            if plan == 100 and cls[ci]["P"] == 128:
+                # on chip the P = 128 rows are half-length real transforms, on the
+                # global path complex row pairs: equal to rounding, not bit for bit
+                assert (out - ref).abs().max().item() <= 1e-6, (ci, plan)
+            else:
+                assert torch.equal(out, ref), (ci, plan)
     assert tried >= 10
 
 
