@@ -364,10 +364,13 @@ int nd_autotune_group(nd_handle *const *handles, const int *methods, int n, doub
                       void *stream);
 /* Force the plan of class cls for a method (-1 default, 0..2 fused variant,
  * 100 global path, 200 cluster of 8 CTAs, 201 cluster of 16 CTAs); ND_ERR_ARG
- * if it does not exist or does not fit.  Plans 0..2 and 100 compute the same arithmetic per element, so
- * trajectories do not depend on which of them runs; the cluster plan splits
- * the column products over the x and y groups and agrees with them to
- * rounding (a few units in the last place of FP32 per step). */
+ * if it does not exist or does not fit.  Plans 0..2 compute the same
+ * arithmetic per element, so trajectories do not depend on which of them
+ * runs; plan 100 does too except at P = 128, where the on-chip kernel
+ * transforms each real row at half length and the global path transforms
+ * pairs of rows; the cluster plans split the column products over the x and
+ * y groups.  These agree to rounding (a few units in the last place of FP32
+ * per step). */
 int nd_set_plan(nd_handle *h, int cls, int method, int plan);
 int nd_plan_info(const nd_handle *h, int cls, int *P, int *n_replicas, int *plan_rk4, int *plan_heun, int *threads_rk4,
                  int *threads_heun);
