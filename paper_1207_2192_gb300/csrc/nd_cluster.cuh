@@ -220,8 +220,10 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
         while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(r.cells + mid) < (ylo + nloc) * D) lo = mid + 1; else hi = mid; }
         crange[1] = lo;
     }
-    // row tasks of this CTA: xy rows 0..nloc-1, then z pairs (0,1), (2,3), ...
-    const int nrt = nloc + (nloc + 1) / 2;
+    // row tasks of this CTA: one real row per (component, row) at P = 128
+    // (half-length transforms), else xy rows 0..nloc-1, then z pairs (0,1), ...
+    constexpr bool HR = HalfRows<P>::on;
+    const int nrt = HR ? 3 * nloc : nloc + (nloc + 1) / 2;
     const int nrounds = (nrt + NGRP - 1) / NGRP;
     // column task of this group: slot j (column kx = rank SPC + j, slot 0 of
     // rank 0 being the packed pair), component c
@@ -254,6 +256,31 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
                 mbar_expect(mb_row, bytes_row);
             }
             // 1. forward rows of the CTA's own rows, sent to the column owners
+            if constexpr (HR) {
+                for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
+                    const bool act = q < nrt;
+                    const int c = act ? q / nloc : 0, l = act ? q - c * nloc : 0, y = ylo + l;
+                    cplx<T> v[FFTGeom<P / 2>::R1];
+                    T xm;
+                    row_fwd_half_spectrum<P, T>(act, msl + c * lms + (long long)l * Dpad, D, v, xm, gid.t, scr, tw,
+                                                gid.gmask);
+                    if (act) {
+#pragma unroll
+                        for (int o = 0; o < FFTGeom<P / 2>::R1; ++o) {
+                            const int k = gid.t + G * o;   // k = 0 goes with k = P/2 into the packed slot
+                            const int ow = k / SPC, j = k - ow * SPC;
+                            const cplx<T> a = k == 0 ? cplx<T>{v[o].x, xm} : v[o];
+                            const int i = (c * (P / 2) + y) * SW + j;
+                            if (ow == rank) {
+                                colbuf[i] = a;
+                            } else {
+                                st_async(cluster_addr(smem_addr(colbuf), ow) + (uint32_t)(i * sizeof(cplx<T>)), a,
+                                         cluster_addr(mb_col, ow));
+                            }
+                        }
+                    }
+                }
+            } else
             for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
                 const bool isxy = q < nloc;
@@ -406,6 +433,14 @@ __global__ void __launch_bounds__(ClusterGeom<P, T, NC>::NT, 1)
             __syncthreads();
             ++phase;
             // 5. inverse rows of the CTA's own rows (the field rows, in place)
+            if constexpr (HR) {
+                for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
+                    const bool act = q < nrt;
+                    const int c = act ? q / nloc : 0, l = act ? q - c * nloc : 0;
+                    cplx<T> *row = spec + c * lcs + (long long)l * RS;
+                    row_inv_half<P, T>(act, row, D, reinterpret_cast<T *>(row), gid.t, scr, tw, gid.gmask);
+                }
+            } else
             for (int q = gid.group; q < nrounds * NGRP; q += NGRP) {
                 const bool act = q < nrt;
                 const bool isxy = q < nloc;

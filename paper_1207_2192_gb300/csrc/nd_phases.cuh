@@ -469,14 +469,13 @@ __device__ __forceinline__ void row_inv_task(int q, bool active, int D, cplx<T> 
 template <int P> struct HalfRows { static constexpr bool on = false; };
 template <> struct HalfRows<128> { static constexpr bool on = FFTGeom<64>::G == FFTGeom<128>::G; };
 
-// Forward: the real row x (x[i], i < D; zero beyond) to its half spectrum
-// X[0..M] in dst.
+// Forward: the real row x (x[i], i < D; zero beyond) to its half spectrum:
+// X[k] for k = t + G o (k < M) left in v[o], X[M] (real) in xm on lane t = 0.
 template <int P, typename T>
-__device__ __forceinline__ void row_fwd_half(bool active, const T *x, int D, cplx<T> *dst, int t, cplx<T> *scr,
-                                             const cplx<T> *twP, unsigned gmask)
+__device__ __forceinline__ void row_fwd_half_spectrum(bool active, const T *x, int D, cplx<T> *v, T &xm, int t,
+                                                      cplx<T> *scr, const cplx<T> *twP, unsigned gmask)
 {
     constexpr int M = P / 2, G = FFTGeom<M>::G, R1 = FFTGeom<M>::R1;
-    cplx<T> v[R1];
 #pragma unroll
     for (int o = 0; o < R1; ++o) v[o] = {T(0), T(0)};
 #pragma unroll
@@ -490,21 +489,35 @@ __device__ __forceinline__ void row_fwd_half(bool active, const T *x, int D, cpl
     fft_group<M, -1, FFT_HALF_IN, 2 * G>(v, t, scr, twP, gmask);
     mirror_put<M>(v, scr, t);
     __syncwarp(gmask);
-    if (active) {
-        const cplx<T> w1 = twP[G + t];   // W^t
-        const T h = T(0.5);
+    const cplx<T> w1 = twP[G + t];   // W^t
+    const T h = T(0.5);
+    xm = v[0].x - v[0].y;            // X[M] = Re Z[0] - Im Z[0] (used on lane 0)
 #pragma unroll
-        for (int o = 0; o < R1; ++o) {
-            const int k = t + G * o;
-            const cplx<T> z = v[o], zm = mirror_get<M>(scr, k);
-            const cplx<T> e = {h * (z.x + zm.x), h * (z.y - zm.y)};   // (Z[k] + conj Z[M-k]) / 2
-            const cplx<T> d = {h * (z.x - zm.x), h * (z.y + zm.y)};   // (Z[k] - conj Z[M-k]) / 2
-            const cplx<T> wd = cmul(twid<-1>(w1, o, P / G), d);        // W^k d, W^k = W^t W^(G o)
-            dst[k] = {e.x + wd.y, e.y - wd.x};                          // e - i W^k d
-        }
-        if (t == 0) dst[M] = {v[0].x - v[0].y, T(0)};
+    for (int o = 0; o < R1; ++o) {
+        const int k = t + G * o;
+        const cplx<T> z = v[o], zm = mirror_get<M>(scr, k);
+        const cplx<T> e = {h * (z.x + zm.x), h * (z.y - zm.y)};   // (Z[k] + conj Z[M-k]) / 2
+        const cplx<T> d = {h * (z.x - zm.x), h * (z.y + zm.y)};   // (Z[k] - conj Z[M-k]) / 2
+        const cplx<T> wd = cmul(twid<-1>(w1, o, P / G), d);        // W^k d, W^k = W^t W^(G o)
+        v[o] = {e.x + wd.y, e.y - wd.x};                            // e - i W^k d
     }
     __syncwarp(gmask);
+}
+
+// Forward, stored: X[0..M] of the real row to dst.
+template <int P, typename T>
+__device__ __forceinline__ void row_fwd_half(bool active, const T *x, int D, cplx<T> *dst, int t, cplx<T> *scr,
+                                             const cplx<T> *twP, unsigned gmask)
+{
+    constexpr int M = P / 2, G = FFTGeom<M>::G, R1 = FFTGeom<M>::R1;
+    cplx<T> v[R1];
+    T xm;
+    row_fwd_half_spectrum<P, T>(active, x, D, v, xm, t, scr, twP, gmask);
+    if (active) {
+#pragma unroll
+        for (int o = 0; o < R1; ++o) dst[t + G * o] = v[o];
+        if (t == 0) dst[M] = {xm, T(0)};
+    }
 }
 
 // Inverse: the half spectrum X[0..M] in src to the real row, x[i] for i < D
