@@ -1,14 +1,15 @@
 // nd_cluster.cuh -- one replica's time steps on a thread-block cluster of NC
 // CTAs (one per SM): for the sizes P <= 128 when a class has too few replicas
-// to fill the GPU with one CTA each, and for P = 256, whose spectrum fits in
-// the shared memory of 16 CTAs but not of one.
+// to fill the GPU with one CTA each, and for P = 192 and 256, whose spectra
+// fit in the shared memory of 16 CTAs but not of one.
 //
 // The replica's rows are split over the cluster: CTA k owns rows
 // [k rpc, (k+1) rpc) of the disk (rpc even, so z row pairs stay whole) and
 // the column slots [k spc, (k+1) spc) of the P/2 slots of the half spectrum
 // (slot 0: the real columns kx = 0 and P/2 packed as one complex column).
 // Per field evaluation (Section II.B convolution):
-//   1. forward rows: each CTA transforms its own rows and stores every
+//   1. forward rows: each CTA transforms its own rows (at P = 128 one real
+//      row per task at half length, else row pairs) and stores every
 //      spectrum entry straight into the shared memory of the CTA that owns
 //      its column (st.async into distributed shared memory, counted on the
 //      owner's transaction barrier: no thread waits on a remote load or on
