@@ -48,6 +48,13 @@ template <typename T> __device__ __forceinline__ vec3<T> heun_dm(vec3<T> m, vec3
     return cross3(m, vec3<T>{g.x - alpha * p.x, g.y - alpha * p.y, g.z - alpha * p.z});
 }
 
+// Programmatic dependent launch: the global path's kernels are launched so
+// that each may start while its predecessor in the stream drains; before it
+// reads anything the predecessor wrote (or the parameter blocks) it waits
+// here until that grid has completed and its writes are visible.  Without
+// the launch attribute this is a no-op.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T> struct V3Ptr {
     T *p;
     long long s;  // component stride
@@ -541,9 +548,11 @@ __global__ void __launch_bounds__(NT, RowsMinB<P, T>::v)
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
+    const int tid = threadIdx.x;
+    load_twiddles<P>(tw, twP, tid, NT);   // constant: before the wait
+    wait_prior_grid();
     const Replica r = reps[work[blockIdx.y]];
-    const int D = r.D, tid = threadIdx.x;
-    load_twiddles<P>(tw, twP, tid, NT);
+    const int D = r.D;
     __syncthreads();
     GroupId<P> gid(tid);
     const int q = blockIdx.x * NGRP + gid.group;
@@ -571,9 +580,11 @@ __global__ void __launch_bounds__(NT)
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
+    const int tid = threadIdx.x;
+    load_twiddles<P>(tw, twP, tid, NT);   // constant: before the wait
+    wait_prior_grid();
     const Replica r = reps[work[blockIdx.y]];
-    const int D = r.D, tid = threadIdx.x;
-    load_twiddles<P>(tw, twP, tid, NT);
+    const int D = r.D;
     __syncthreads();
     GroupId<P> gid(tid);
     const int q = blockIdx.x * NGRP + gid.group;
@@ -616,7 +627,8 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
     const int tid = threadIdx.x;
-    load_twiddles<P>(tw, twP, tid, NT);
+    load_twiddles<P>(tw, twP, tid, NT);   // constant: before the wait
+    wait_prior_grid();
     GroupId<P> gid(tid);
     const int g = gid.group, j = g & 3, c = XY ? (g >> 2) : 2, t = gid.t;
     cplx<T> *scr = scratch + g * SCR;
@@ -794,6 +806,7 @@ __global__ void __launch_bounds__(256)
 {
     constexpr int RS = SpecGeom<P>::RS;
     static_assert(RS % 2 == 0, "field rows start on 16-byte boundaries");
+    wait_prior_grid();
     const Replica &r = reps[work[blockIdx.y]];
     const int D = r.D, Dpad = r.Dpad, qpr = Dpad / 4;
     const int qd = blockIdx.x * 256 + threadIdx.x;
@@ -860,6 +873,7 @@ template <typename T>
 __global__ void k_g_load_stage(const Replica *__restrict__ reps, const int *__restrict__ work, const T *__restrict__ ybase,
                                T *__restrict__ msbase)
 {
+    wait_prior_grid();
     const Replica r = reps[work[blockIdx.y]];
     const int D = r.D, DD = D * D;
     const long long ms_s = (long long)D * r.Dpad;
@@ -1201,6 +1215,24 @@ static void launch_g_epi(const LaunchArgs &a, dim3 ge, int stage, unsigned long 
                                                    (const cplx<T> *)a.spec, a.red, stage, step);
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while its predecessor finishes, and waits for it in wait_prior_grid().
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // The stepping epilogue with quad access when the state buffers allow it.
 template <int P, typename T, int MODE>
 static void launch_g_epi_step(const LaunchArgs &a, int maxD, int stage, unsigned long long step)
@@ -1209,8 +1241,8 @@ static void launch_g_epi_step(const LaunchArgs &a, int maxD, int stage, unsigned
                         reinterpret_cast<uintptr_t>(a.acc)) & 15) == 0;
     if (quad) {
         const int maxq = maxD * ((maxD + 3) / 4);
-        k_g_epi_quad<P, T, MODE><<<dim3((maxq + 255) / 256, a.nwork), 256, 0, a.stream>>>(
-            a.reps, a.work, (T *)a.ms, (T *)a.y, (T *)a.acc, (const cplx<T> *)a.spec, stage, step);
+        launch_pdl(k_g_epi_quad<P, T, MODE>, dim3((maxq + 255) / 256, a.nwork), dim3(256), 0, a.stream, a.reps,
+                   a.work, (T *)a.ms, (T *)a.y, (T *)a.acc, (const cplx<T> *)a.spec, stage, step);
     } else {
         launch_g_epi<P, T, MODE>(a, dim3((maxD * maxD + 255) / 256, a.nwork), stage, step);
     }
@@ -1225,9 +1257,8 @@ static void glob_rows(const LaunchArgs &a, int maxD, int inverse)
     constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
     const int nrow = row_tasks(maxD);
     dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork);
-    k_g_rows<P, T, NT><<<gr, NT, glob_smem_bytes<P, T, NT>(), a.stream>>>(a.reps, a.work, (const T *)a.ms,
-                                                                       (cplx<T> *)a.spec, (const cplx<T> *)a.tw,
-                                                                       inverse);
+    launch_pdl(k_g_rows<P, T, NT>, gr, dim3(NT), glob_smem_bytes<P, T, NT>(), a.stream, a.reps, a.work,
+               (const T *)a.ms, (cplx<T> *)a.spec, (const cplx<T> *)a.tw, inverse);
 }
 
 template <int P, typename T>
@@ -1240,14 +1271,14 @@ static void glob_cols(const LaunchArgs &a, int maxD)
         const int ntask = a.nwork * CX::NCB;
         const int gx = ntask < a.n_sm * CX::MINB ? ntask : a.n_sm * CX::MINB;
         const int gz = ntask < a.n_sm * CZ::MINB ? ntask : a.n_sm * CZ::MINB;
-        k_g_cols_tile<P, T, true><<<gx, CX::NT, glob_smem_bytes<P, T, CX::NT>(), a.stream>>>(
-            a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
-        k_g_cols_tile<P, T, false><<<gz, CZ::NT, glob_smem_bytes<P, T, CZ::NT>(), a.stream>>>(
-            a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+        launch_pdl(k_g_cols_tile<P, T, true>, dim3(gx), dim3(CX::NT), glob_smem_bytes<P, T, CX::NT>(), a.stream,
+                   a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
+        launch_pdl(k_g_cols_tile<P, T, false>, dim3(gz), dim3(CZ::NT), glob_smem_bytes<P, T, CZ::NT>(), a.stream,
+                   a.reps, a.work, a.nwork, (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
     } else {
         dim3 gc((P / 2 + NGRP - 1) / NGRP, a.nwork);
-        k_g_cols<P, T, NT><<<gc, NT, glob_smem_bytes<P, T, NT>(), a.stream>>>(a.reps, a.work, (cplx<T> *)a.spec,
-                                                                             (const cplx<T> *)a.tw);
+        launch_pdl(k_g_cols<P, T, NT>, gc, dim3(NT), glob_smem_bytes<P, T, NT>(), a.stream, a.reps, a.work,
+                   (cplx<T> *)a.spec, (const cplx<T> *)a.tw);
     }
 }
 
@@ -1293,7 +1324,7 @@ static cudaError_t launch_global_p(const LaunchArgs &a, int maxD)
     if (e0 != cudaSuccess) return e0;
 
     dim3 gl((maxD * maxD + 255) / 256, a.nwork);
-    k_g_load_stage<T><<<gl, 256, 0, a.stream>>>(a.reps, a.work, (const T *)a.y, (T *)a.ms);
+    launch_pdl(k_g_load_stage<T>, gl, dim3(256), 0, a.stream, a.reps, a.work, (const T *)a.y, (T *)a.ms);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.mode == M_RELAX) {
