@@ -601,8 +601,8 @@ __global__ void __launch_bounds__(NT)
 // between the spectrum and the groups' scratch areas as row-contiguous runs
 // of four complex words (one 32-byte sector per row: rows start on sectors,
 // SpecGeom::RS), so every sector the pass reads or writes is used whole.  The
-// packed real columns kx = 0, P/2 (group j = 0 of block 0) move their two
-// columns themselves.  Persistent grid over (replica, column block) tasks.
+// packed real columns kx = 0, P/2 are group j = 0 of block 0.  Persistent
+// grid over (replica, column block) tasks.
 template <int P, typename T, bool XY> struct ColTile {
     static constexpr int G = FFTGeom<P>::G;
     static constexpr int NCOMP = XY ? 2 : 1;
@@ -612,6 +612,14 @@ template <int P, typename T, bool XY> struct ColTile {
     // resident CTAs per SM the kernel is compiled for: 16 warps at 128
     // registers (FP64 columns take twice the registers)
     static constexpr int MINB = sizeof(T) == 8 ? 1 : 512 / NT;
+    // How the packed pair is transformed.  With 32 points per thread (P = 512,
+    // 1024) a second inlined transform for it pushes the kernel past its 128
+    // registers (96-124 bytes of spills per thread in FP32), so the pair moves
+    // through the tile like the other columns and runs the same transform
+    // calls; with 16 or 24 points per thread nothing spills, and the pair
+    // loads, transforms and stores its two columns itself, which measured 3%
+    // faster at P = 256.
+    static constexpr bool SHARED_PACKED = FFTGeom<P>::R1 >= 32;
 };
 
 template <int P, typename T, bool XY>
@@ -622,6 +630,7 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
     using Gm = FFTGeom<P>;
     using CT = ColTile<P, T, XY>;
     constexpr int G = Gm::G, R1 = Gm::R1, KH = SpecGeom<P>::KH, RS = SpecGeom<P>::RS, NT = CT::NT, SCR = Gm::SCRATCH;
+    constexpr bool SP = CT::SHARED_PACKED;
     static_assert(RS % 4 == 0, "rows start on 32-byte sectors");
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
@@ -644,18 +653,26 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
         const int kx = packed ? 1 : kx0 + j;   // (the packed group reads no kx column of the table)
         __syncthreads();   // twiddles filled / the previous task's tiles stored
         // tile load: thread -> column jj = tid & 3 of the block, rows tid/4 + k NT/4
+        // (column 0 of block 0: the packed pair c_0 + i c_{P/2}, when it moves
+        // through the tile)
         const int cbase = XY ? 0 : 2, jj = tid & 3;
-        if (!(cb == 0 && jj == 0)) {
+        const bool ppair = cb == 0 && jj == 0;
+        if (SP || !ppair) {
 #pragma unroll
             for (int ci = 0; ci < CT::NCOMP; ++ci) {
                 const cplx<T> *src = spec + (cbase + ci) * cs + kx0 + jj;
                 cplx<T> *dst = scratch + (4 * ci + jj) * SCR;
-                for (int y = tid >> 2; y < D; y += NT / 4) dst[y] = src[(long long)y * RS];
+                if (SP && ppair) {
+                    for (int y = tid >> 2; y < D; y += NT / 4)
+                        dst[y] = {src[(long long)y * RS].x, src[(long long)y * RS + P / 2].x};
+                } else {
+                    for (int y = tid >> 2; y < D; y += NT / 4) dst[y] = src[(long long)y * RS];
+                }
             }
         }
         __syncthreads();
         cplx<T> v[R1];
-        if (packed) {
+        if (!SP && packed) {
             packed_col_fwd<P, T>(v, c, true, D, spec + c * cs, Ghat, t, gid.lane, scr, tw, gid.gmask);
         } else {
 #pragma unroll
@@ -673,7 +690,10 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
             }
         }
         if (XY) __syncthreads();
-        if (!packed) {
+        if (packed) {
+            // (the packed pair's partner is packed too and reads no spectrum of it)
+            if (SP) packed_col_scale<P, T>(v, c, Ghat, t, scr, gid.gmask);
+        } else {
             // the component-major copy of the table: each group reads only the
             // entries it uses (4 or 8 bytes per point instead of 16)
             constexpr int KK = KH * KH;
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
         if (XY) __syncthreads();   // the partner's spectrum is read before the scratch is reused
         fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gid.gmask);
         __syncwarp(gid.gmask);
-        if (packed) {
+        if (!SP && packed) {
             packed_col_store<P, T>(v, true, D, spec + c * cs, t);
         } else {
 #pragma unroll
@@ -713,12 +733,20 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
             }
         }
         __syncthreads();
-        if (!(cb == 0 && jj == 0)) {
+        if (SP || !ppair) {
 #pragma unroll
             for (int ci = 0; ci < CT::NCOMP; ++ci) {
                 cplx<T> *dst = spec + (cbase + ci) * cs + kx0 + jj;
                 const cplx<T> *src = scratch + (4 * ci + jj) * SCR;
-                for (int y = tid >> 2; y < D; y += NT / 4) dst[(long long)y * RS] = src[y];
+                if (SP && ppair) {
+                    for (int y = tid >> 2; y < D; y += NT / 4) {
+                        const cplx<T> u = src[y];
+                        dst[(long long)y * RS] = {u.x, T(0)};
+                        dst[(long long)y * RS + P / 2] = {u.y, T(0)};
+                    }
+                } else {
+                    for (int y = tid >> 2; y < D; y += NT / 4) dst[(long long)y * RS] = src[y];
+                }
             }
         }
     }
