@@ -1,6 +1,10 @@
 """torch.autograd wrappers of the micromagnetic energy and of the force
 constant, and a constrained relaxation driven by the energy's gradient.
 
+Equations are cited by the paper's own labels: Eq. Hmm is the effective 2D
+Hamiltonian, Eq. Bi the local induction as minus its gradient, Eq. Ux the
+parabolic energy of a displaced core that defines k_F.
+
 ``EnergyFn.apply(m, L, disk_handle)`` returns the energy in joules of every
 replica of a single-disk ``Nanodisk`` (the energy of Eq. Hmm, Sec. II.A, with
 an FP64 field and FP64 sums in the library).  Its backward calls the library
