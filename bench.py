@@ -427,22 +427,36 @@ def uneven_record(steps, warmup, world, local_rank, dist, flush):
         dist.barrier()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
     value = whole_job_rate(cells * CHUNK * steps, world, total_ms / 1e3)
-    # end to end: both handles stepped through the C ABI on pinned host buffers
     hosts = {}
     for name in groups:
         hosts[name] = torch.empty(hs[name].state_elems, dtype=torch.float32, pin_memory=True)
         hosts[name].copy_(ms[name].cpu())
+    nbytes = sum(x.numel() * x.element_size() for x in hosts.values())
+    e2e_steps = max(3, steps // 4)
+    # end to end as the joined graph is used: every step both handles' states
+    # go in from pinned host memory, one graph launch steps them, and they come
+    # back to the host before the next step
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e2e_steps = max(3, steps // 4)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        for name in groups:
+            ms[name].copy_(hosts[name], non_blocking=True)
+        nd.nd_graph_launch(g, stream)
+        for name in groups:
+            hosts[name].copy_(ms[name], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    # the same through the stepping calls on host buffers, one handle after the other
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         nd.nd_step_rk4(hs["rk4"].h, hosts["rk4"].data_ptr(), CHUNK, DT, None)
         _, Tk, sd = args_by["heun"]
         nd.nd_step_heun(hs["heun"].h, hosts["heun"].data_ptr(), CHUNK, DT, Tk, sd, 1000 * CHUNK + i * CHUNK, None)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    nbytes = sum(x.numel() * x.element_size() for x in hosts.values())
+    calls_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     nd.nd_graph_destroy(g)
     for x in gs.values():
         nd.nd_graph_destroy(x)
@@ -457,7 +471,12 @@ def uneven_record(steps, warmup, world, local_rank, dist, flush):
                                "plans from nd_autotune_group",
                    "l2": "flushed between timed steps (256 MB write)"},
         "e2e": {"value": whole_job_rate(cells * CHUNK * e2e_steps, world, e2e_s), "unit": "cell-updates/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "path": "pinned host -> device copies, nd_graph_launch of the joined graph, device -> host copies, "
+                        "synchronised every step",
+                "step_calls_value": whole_job_rate(cells * CHUNK * e2e_steps, world, calls_s),
+                "step_calls_path": "nd_step_rk4 then nd_step_heun on the pinned host buffers (the C ABI stages "
+                                   "each handle's copies itself; the handles run one after the other)"},
         "gpu_launches": launches_per_step * steps, "clocks": clk.summary(),
     }
 
