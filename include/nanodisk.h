@@ -25,7 +25,7 @@
  * side.  Cell (i, j) (column i = x index, row j = y index) has its centre at
  * ((i - (D-1)/2) a, (j - (D-1)/2) a) and belongs to the disk iff that centre
  * lies within R.  The FFT grid side P is the smallest power of two >= 2D - 1
- * (at least 16; 192 instead of 256 with ND_GRID_3X), which makes the circular
+ * (at least 16; 192 or 200 instead of 256 with ND_GRID_3X), which makes the circular
  * convolution equal the linear one.
  *
  * State layout.  One handle holds B replicas (disk-major: the replicas of disk
@@ -71,7 +71,8 @@ extern "C" {
 #define ND_METHOD_HEUN 1
 #define ND_FP64 1               /* double everywhere */
 #define ND_GRID_3X 0x100        /* nd_create_disk flag (or-ed into precision): allow the padded
-                                   size 192 = 3 * 64 for disks of 65..96 cells (see there) */
+                                   sizes 192 = 3 * 64 for disks of 65..96 cells and
+                                   200 = 8 * 25 for 97..100 cells (see there) */
 
 typedef struct nd_handle nd_handle;
 
@@ -95,9 +96,11 @@ typedef struct {
  * a/sqrt(pi)) with the exchange stencil folded in.  Requires D >= 1 and
  * P <= 1024.  precision is ND_FP32 or ND_FP64, optionally or-ed with
  * ND_GRID_3X: then disks of 65..96 cells get the padded grid P = 192 = 8 x 24
- * (an FFT with one radix-3 stage) instead of 256 -- any P >= 2D - 1 makes the
- * circular convolution equal the linear one; the paper's power-of-two rule
- * (Sec. II.B) is a convenience -- with 44% fewer spectral points.  On success
+ * (an FFT with one radix-3 stage) and disks of 97..100 cells P = 200 = 10 x 20
+ * (radix-5 stages, ten-lane FFT groups) instead of 256 -- any P >= 2D - 1 makes
+ * the circular convolution equal the linear one; the paper's power-of-two rule
+ * (Sec. II.B) is a convenience -- with 44% and 39% fewer spectral points.
+ * P = 200 runs on the global path only (no cluster plan).  On success
  * *out receives the handle; the call synchronises the current device. */
 int nd_create_disk(const nd_disk_desc *disks, int n_disks, const int *replicas_per_disk, int precision,
                    nd_handle **out);

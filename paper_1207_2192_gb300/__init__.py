@@ -61,7 +61,8 @@ class Nanodisk:
     """One library handle: disks, replicas and their state layout."""
 
     def __init__(self, disks, replicas=None, precision=ND_FP32, grid3x=False):
-        """grid3x: allow the padded size 192 (3 x 64) for disks of 65..96 cells."""
+        """grid3x: allow the padded sizes 192 (3 x 64) for disks of 65..96 cells
+        and 200 (8 x 25) for disks of 97..100 cells."""
         disks = list(disks) if isinstance(disks, (list, tuple)) else [disks]
         self.disks = disks
         self.precision = precision

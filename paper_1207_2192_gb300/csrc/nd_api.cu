@@ -95,11 +95,13 @@ int next_pow2_at_least(int n)
 }
 
 // Padded FFT side for a linear convolution of span n = 2D - 1: the next power
-// of two, or with ND_GRID_3X the 3 * 2^n size 192 where it is smaller.
+// of two, or with ND_GRID_3X the smallest of the register FFT's other sizes
+// where it is smaller: 192 = 3 * 2^6 (n <= 192) and 200 = 2^3 * 5^2 (n <= 200).
 int padded_size(int n, bool allow3)
 {
     const int p2 = next_pow2_at_least(n);
     if (allow3 && n <= 192 && p2 > 192) return 192;
+    if (allow3 && n <= 200 && p2 > 200) return 200;
     return p2;
 }
 

@@ -10,22 +10,27 @@
 //   3. one transpose through a padded per-group shared scratch area,
 //   4. R1/G G-point DFTs in registers,
 // so every point crosses shared memory exactly once.  Register DFTs are
-// radix-2 decimation in time with compile-time twiddles from the constant bank.
+// radix-2 decimation in time, with one radix-3 or radix-5 stage on top for the
+// sizes with those factors, and compile-time twiddles from the constant bank.
+// G need not divide the warp: with G = 10 a warp holds three groups and its
+// last two lanes idle.
 #pragma once
 #include "nd_common.cuh"
 
 namespace nd {
 
-// 32nd roots of unity exp(-2 pi i k / 32), k = 0..31, and 24th roots
+// 32nd roots of unity exp(-2 pi i k / 32), k = 0..31, 24th roots
 // exp(-2 pi i k / 24), k = 0..23 (for the stages of transforms with a factor
-// 3), in the constant bank.  Each translation unit that includes this header
-// owns a copy, filled by its own upload hook (ND_DEFINE_TWIDDLE_UPLOAD).
-// Indices are compile-time constants in the register DFTs, so each use becomes
-// a constant-bank operand.
+// 3) and 20th roots exp(-2 pi i k / 20), k = 0..19 (factor 5), in the constant
+// bank.  Each translation unit that includes this header owns a copy, filled
+// by its own upload hook (ND_DEFINE_TWIDDLE_UPLOAD).  Indices are compile-time
+// constants in the register DFTs, so each use becomes a constant-bank operand.
 static __constant__ float2 c_w32f[32];
 static __constant__ double2 c_w32d[32];
 static __constant__ float2 c_w24f[24];
 static __constant__ double2 c_w24d[24];
+static __constant__ float2 c_w20f[20];
+static __constant__ double2 c_w20d[20];
 
 template <typename T> __device__ __forceinline__ cplx<T> w32(int k);
 template <> __device__ __forceinline__ cplx<float> w32<float>(int k) { float2 v = c_w32f[k]; return {v.x, v.y}; }
@@ -33,8 +38,11 @@ template <> __device__ __forceinline__ cplx<double> w32<double>(int k) { double2
 template <typename T> __device__ __forceinline__ cplx<T> w24(int k);
 template <> __device__ __forceinline__ cplx<float> w24<float>(int k) { float2 v = c_w24f[k]; return {v.x, v.y}; }
 template <> __device__ __forceinline__ cplx<double> w24<double>(int k) { double2 v = c_w24d[k]; return {v.x, v.y}; }
+template <typename T> __device__ __forceinline__ cplx<T> w20(int k);
+template <> __device__ __forceinline__ cplx<float> w20<float>(int k) { float2 v = c_w20f[k]; return {v.x, v.y}; }
+template <> __device__ __forceinline__ cplx<double> w20<double>(int k) { double2 v = c_w20d[k]; return {v.x, v.y}; }
 
-// re/im: the 32 roots exp(-2 pi i k/32); the 24 roots are computed here.
+// re/im: the 32 roots exp(-2 pi i k/32); the 24 and 20 roots are computed here.
 #define ND_DEFINE_TWIDDLE_UPLOAD(name)                                                  \
     cudaError_t name(const double *re, const double *im)                                \
     {                                                                                   \
@@ -44,18 +52,25 @@ template <> __device__ __forceinline__ cplx<double> w24<double>(int k) { double2
             f[k] = make_float2((float)re[k], (float)im[k]);                             \
             d[k] = make_double2(re[k], im[k]);                                          \
         }                                                                               \
-        float2 f24[24];                                                                 \
-        double2 d24[24];                                                                \
+        float2 f24[24], f20[20];                                                        \
+        double2 d24[24], d20[20];                                                       \
         for (int k = 0; k < 24; ++k) {                                                  \
             const double c = cos(2.0 * M_PI * k / 24.0), s = -sin(2.0 * M_PI * k / 24.0); \
             f24[k] = make_float2((float)c, (float)s);                                   \
             d24[k] = make_double2(c, s);                                                \
         }                                                                               \
+        for (int k = 0; k < 20; ++k) {                                                  \
+            const double c = cos(2.0 * M_PI * k / 20.0), s = -sin(2.0 * M_PI * k / 20.0); \
+            f20[k] = make_float2((float)c, (float)s);                                   \
+            d20[k] = make_double2(c, s);                                                \
+        }                                                                               \
         cudaError_t e = cudaMemcpyToSymbol(c_w32f, f, sizeof(f));                        \
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32d, d, sizeof(d));             \
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w24f, f24, sizeof(f24));         \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w24d, d24, sizeof(d24));         \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w20f, f20, sizeof(f20));         \
         if (e != cudaSuccess) return e;                                                 \
-        return cudaMemcpyToSymbol(c_w24d, d24, sizeof(d24));                            \
+        return cudaMemcpyToSymbol(c_w20d, d20, sizeof(d20));                            \
     }
 
 template <int P> struct FFTShape;
@@ -69,6 +84,9 @@ template <> struct FFTShape<1024> { static constexpr int G = 32; };
 // 192 = 8 x 24 (a radix-3 stage in the 24-point register DFT): the smallest
 // grid of the form 2^n or 3 * 2^n above 128 for disks of 65..96 cells
 template <> struct FFTShape<192> { static constexpr int G = 8; };
+// 200 = 10 x 20 (radix-5 stages in the 20- and 10-point register DFTs) for
+// disks of 97..100 cells: ten-lane groups, three to a warp
+template <> struct FFTShape<200> { static constexpr int G = 10; };
 
 template <int P> struct FFTGeom {
     static constexpr int G = FFTShape<P>::G;
@@ -80,7 +98,8 @@ template <int P> struct FFTGeom {
     static constexpr int SROW = G + 1;
     static constexpr int SRAW = R1 * SROW;
     static constexpr int SCRATCH = SRAW + ((8 - SRAW % 16) + 16) % 16;
-    static constexpr int GROUPS_PER_WARP = 32 / G;
+    static constexpr int GROUPS_PER_WARP = 32 / G;   // whole groups per warp
+    static constexpr bool POW2 = (G & (G - 1)) == 0;   // groups tile the warp exactly
 };
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
@@ -92,9 +111,9 @@ __host__ __device__ constexpr int bitrev(int i, int bits)
 }
 
 // b * w^k for the N-th root w = exp(DIR 2 pi i / N) (DIR = -1 forward), N a
-// power of two up to 32 or a divisor of 24, with the trivial factors 1, -1
-// and -+i special-cased; k and N are constants after the register DFT loops
-// are unrolled, so the branches fold away.
+// power of two up to 32 or a divisor of 24 or of 20, with the trivial factors
+// 1, -1 and -+i special-cased; k and N are constants after the register DFT
+// loops are unrolled, so the branches fold away.
 template <int DIR, typename T>
 __device__ __forceinline__ cplx<T> twid(cplx<T> b, int k, int N)
 {
@@ -105,13 +124,14 @@ __device__ __forceinline__ cplx<T> twid(cplx<T> b, int k, int N)
         return DIR < 0 ? cplx<T>{b.y, -b.x} : cplx<T>{-b.y, b.x};
     }
     if (4 * k == 3 * N) return DIR < 0 ? cplx<T>{-b.y, b.x} : cplx<T>{b.y, -b.x};
-    cplx<T> w = (32 % N == 0) ? w32<T>(k * (32 / N)) : w24<T>(k * (24 / N));
+    cplx<T> w = (32 % N == 0) ? w32<T>(k * (32 / N)) : (24 % N == 0) ? w24<T>(k * (24 / N)) : w20<T>(k * (20 / N));
     return DIR < 0 ? cmul(b, w) : cmulc(b, w);
 }
 
 // In-register N-point DFT, natural order in and out:
 // v[k] <- sum_n v[n] exp(DIR 2 pi i n k / N), for N a power of two up to 32
-// (radix 2) or three times one (one radix-3 stage on top, N | 24).
+// (radix 2), or three or five times one (one radix-3 stage on top, N | 24, or
+// one radix-5 stage, N | 20).
 template <int N, int DIR, typename T>
 __device__ __forceinline__ void dft_reg(cplx<T> *v)
 {
@@ -135,8 +155,46 @@ __device__ __forceinline__ void dft_reg(cplx<T> *v)
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) v[i] = u[i];
+    } else if constexpr (N % 5 == 0) {
+        static_assert(20 % N == 0, "register DFT sizes: 2^n <= 32 or divisors of 24 or of 20");
+        // decimation in time by 5: five N/5-point DFTs of the residues n = 5m + r,
+        // then N/5 five-point butterflies over r of w_N^{rk} A_r[k]; with
+        // c_j = cos(2 pi j/5), s_j = sin(2 pi j/5) and DIR i = exp(DIR i pi/2):
+        //   X[k]      = b0 + (b1 + b4) + (b2 + b3)
+        //   X[k +  M] = p1 + DIR i q1,  X[k + 4M] = p1 - DIR i q1
+        //   X[k + 2M] = p2 + DIR i q2,  X[k + 3M] = p2 - DIR i q2
+        // p1 = b0 + c1 (b1 + b4) + c2 (b2 + b3),  q1 = s1 (b1 - b4) + s2 (b2 - b3)
+        // p2 = b0 + c2 (b1 + b4) + c1 (b2 + b3),  q2 = s2 (b1 - b4) - s1 (b2 - b3)
+        constexpr int M = N / 5;
+        cplx<T> a[5][M];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int r = 0; r < 5; ++r) a[r][m] = v[5 * m + r];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) dft_reg<M, DIR>(a[r]);
+        const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);   // cos(2 pi/5), cos(4 pi/5)
+        const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);    // sin(2 pi/5), sin(4 pi/5)
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const cplx<T> b0 = a[0][k], b1 = twid<DIR>(a[1][k], k, N), b2 = twid<DIR>(a[2][k], 2 * k, N),
+                          b3 = twid<DIR>(a[3][k], 3 * k, N), b4 = twid<DIR>(a[4][k], 4 * k, N);
+            const cplx<T> t1 = cadd(b1, b4), t2 = cadd(b2, b3), t3 = csub(b1, b4), t4 = csub(b2, b3);
+            const cplx<T> p1 = {b0.x + c1 * t1.x + c2 * t2.x, b0.y + c1 * t1.y + c2 * t2.y};
+            const cplx<T> p2 = {b0.x + c2 * t1.x + c1 * t2.x, b0.y + c2 * t1.y + c1 * t2.y};
+            const cplx<T> q1 = {s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+            const cplx<T> q2 = {s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+            // DIR i q = DIR (-q.y, q.x)
+            const cplx<T> e1 = DIR < 0 ? cplx<T>{q1.y, -q1.x} : cplx<T>{-q1.y, q1.x};
+            const cplx<T> e2 = DIR < 0 ? cplx<T>{q2.y, -q2.x} : cplx<T>{-q2.y, q2.x};
+            v[k] = cadd(b0, cadd(t1, t2));
+            v[k + M] = cadd(p1, e1);
+            v[k + 4 * M] = csub(p1, e1);
+            v[k + 2 * M] = cadd(p2, e2);
+            v[k + 3 * M] = csub(p2, e2);
+        }
     } else {
-        static_assert(N % 3 == 0 && 24 % N == 0, "register DFT sizes: 2^n <= 32 or divisors of 24");
+        static_assert(N % 3 == 0 && 24 % N == 0, "register DFT sizes: 2^n <= 32 or divisors of 24 or of 20");
         // decimation in time by 3: three N/3-point DFTs of the residues n = 3m + r,
         // then N/3 three-point butterflies with the twiddles w_N^{rk}
         constexpr int M = N / 3;

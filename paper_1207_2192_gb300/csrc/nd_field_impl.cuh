@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(NT, RowsMinB<P, T>::v)
              cplx<T> *__restrict__ specbase, const cplx<T> *__restrict__ twP, int inverse)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = NT / G;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = groups_per_block<P, NT>();
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
@@ -558,6 +558,7 @@ __global__ void __launch_bounds__(NT, RowsMinB<P, T>::v)
     const int q = blockIdx.x * NGRP + gid.group;
     const int nrow = row_tasks(D);
     if (blockIdx.x * NGRP >= nrow) return;   // CTA-uniform
+    if (!gid.valid) return;                  // lanes past the warp's last group
     const long long cs = (long long)D * RS;
     cplx<T> *spec = specbase + r.spec_off;
     cplx<T> *scr = scratch + gid.group * Gm::SCRATCH;
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(NT)
              const cplx<T> *__restrict__ twP)
 {
     using Gm = FFTGeom<P>;
-    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = NT / G;
+    constexpr int G = Gm::G, R1 = Gm::R1, RS = SpecGeom<P>::RS, NGRP = groups_per_block<P, NT>();
     extern __shared__ __align__(16) unsigned char gsm[];
     cplx<T> *tw = reinterpret_cast<cplx<T> *>(gsm);
     cplx<T> *scratch = tw + R1 * G;
@@ -587,6 +588,7 @@ __global__ void __launch_bounds__(NT)
     const int D = r.D;
     __syncthreads();
     GroupId<P> gid(tid);
+    if (!gid.valid) return;   // lanes past the warp's last group
     const int q = blockIdx.x * NGRP + gid.group;
     const long long cs = (long long)D * RS;
     col_task<P, T>(q, q < P / 2, D, specbase + r.spec_off, cs, reinterpret_cast<const T *>(r.Ghat), gid.t, gid.lane,
@@ -607,7 +609,12 @@ template <int P, typename T, bool XY> struct ColTile {
     static constexpr int G = FFTGeom<P>::G;
     static constexpr int NCOMP = XY ? 2 : 1;
     static constexpr int NG = 4 * NCOMP;
-    static constexpr int NT = NG * G;
+    // whole warps: with ten-lane groups (P = 200, three to a warp) the XY
+    // block is three warps with one group slot and each warp's last two
+    // lanes idle, the Z block two warps with two idle slots
+    static constexpr bool POW2 = FFTGeom<P>::POW2;
+    static constexpr int GPW = FFTGeom<P>::GROUPS_PER_WARP;
+    static constexpr int NT = POW2 ? NG * G : (NG + GPW - 1) / GPW * 32;
     static constexpr int NCB = P / 2 / 4;
     // resident CTAs per SM the kernel is compiled for: 16 warps at 128
     // registers (FP64 columns take twice the registers)
@@ -640,6 +647,9 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
     wait_prior_grid();
     GroupId<P> gid(tid);
     const int g = gid.group, j = g & 3, c = XY ? (g >> 2) : 2, t = gid.t;
+    // a group of the block (idle slots and lanes take part in the tile moves
+    // and the barriers only)
+    const bool gv = CT::POW2 || (gid.valid && g < CT::NG);
     cplx<T> *scr = scratch + g * SCR;
     const cplx<T> *other = scratch + (g ^ 4) * SCR;   // XY only
     for (int task = blockIdx.x; task < nwork * CT::NCB; task += gridDim.x) {
@@ -672,7 +682,8 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
         }
         __syncthreads();
         cplx<T> v[R1];
-        if (!SP && packed) {
+        if (!gv) {
+        } else if (!SP && packed) {
             packed_col_fwd<P, T>(v, c, true, D, spec + c * cs, Ghat, t, gid.lane, scr, tw, gid.gmask);
         } else {
 #pragma unroll
@@ -690,7 +701,8 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
             }
         }
         if (XY) __syncthreads();
-        if (packed) {
+        if (!gv) {
+        } else if (packed) {
             // (the packed pair's partner is packed too and reads no spectrum of it)
             if (SP) packed_col_scale<P, T>(v, c, Ghat, t, scr, gid.gmask);
         } else {
@@ -721,15 +733,17 @@ __global__ void __launch_bounds__(ColTile<P, T, XY>::NT, ColTile<P, T, XY>::MINB
             }
         }
         if (XY) __syncthreads();   // the partner's spectrum is read before the scratch is reused
-        fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gid.gmask);
-        __syncwarp(gid.gmask);
-        if (!SP && packed) {
-            packed_col_store<P, T>(v, true, D, spec + c * cs, t);
-        } else {
+        if (gv) {
+            fft_group<P, +1, FFT_HALF_OUT>(v, t, scr, tw, gid.gmask);
+            __syncwarp(gid.gmask);
+            if (!SP && packed) {
+                packed_col_store<P, T>(v, true, D, spec + c * cs, t);
+            } else {
 #pragma unroll
-            for (int o = 0; o < R1 / 2; ++o) {
-                const int y = t + G * o;
-                if (y < D) scr[y] = v[o];
+                for (int o = 0; o < R1 / 2; ++o) {
+                    const int y = t + G * o;
+                    if (y < D) scr[y] = v[o];
+                }
             }
         }
         __syncthreads();
@@ -1134,7 +1148,8 @@ template <int P> struct GlobTiled { static constexpr bool v = P > 128; };
 template <int P, typename T, int NT>
 constexpr size_t glob_smem_bytes()
 {
-    return sizeof(cplx<T>) * ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G + (size_t)(NT / FFTGeom<P>::G) * FFTGeom<P>::SCRATCH);
+    return sizeof(cplx<T>) *
+           ((size_t)FFTGeom<P>::R1 * FFTGeom<P>::G + (size_t)groups_per_block<P, NT>() * FFTGeom<P>::SCRATCH);
 }
 
 
@@ -1282,7 +1297,7 @@ static void launch_g_epi_step(const LaunchArgs &a, int maxD, int stage, unsigned
 template <int P, typename T>
 static void glob_rows(const LaunchArgs &a, int maxD, int inverse)
 {
-    constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
+    constexpr int NT = GlobNT<P>::v, NGRP = groups_per_block<P, NT>();
     const int nrow = row_tasks(maxD);
     dim3 gr((nrow + NGRP - 1) / NGRP, a.nwork);
     launch_pdl(k_g_rows<P, T, NT>, gr, dim3(NT), glob_smem_bytes<P, T, NT>(), a.stream, a.reps, a.work,
@@ -1292,7 +1307,7 @@ static void glob_rows(const LaunchArgs &a, int maxD, int inverse)
 template <int P, typename T>
 static void glob_cols(const LaunchArgs &a, int maxD)
 {
-    constexpr int NT = GlobNT<P>::v, G = FFTGeom<P>::G, NGRP = NT / G;
+    constexpr int NT = GlobNT<P>::v, NGRP = groups_per_block<P, NT>();
     if constexpr (GlobTiled<P>::v) {
         using CX = ColTile<P, T, true>;
         using CZ = ColTile<P, T, false>;

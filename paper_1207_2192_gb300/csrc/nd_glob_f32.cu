@@ -15,6 +15,7 @@ cudaError_t launch_global_f32(int P, const LaunchArgs &a, int maxD)
     case 64: return launch_global_p<64, float>(a, maxD);
     case 128: return launch_global_p<128, float>(a, maxD);
     case 192: return launch_global_p<192, float>(a, maxD);
+    case 200: return launch_global_p<200, float>(a, maxD);
     case 256: return launch_global_p<256, float>(a, maxD);
     case 512: return launch_global_p<512, float>(a, maxD);
     case 1024: return launch_global_p<1024, float>(a, maxD);

@@ -15,6 +15,7 @@ cudaError_t launch_global_f64(int P, const LaunchArgs &a, int maxD)
     case 64: return launch_global_p<64, double>(a, maxD);
     case 128: return launch_global_p<128, double>(a, maxD);
     case 192: return launch_global_p<192, double>(a, maxD);
+    case 200: return launch_global_p<200, double>(a, maxD);
     case 256: return launch_global_p<256, double>(a, maxD);
     case 512: return launch_global_p<512, double>(a, maxD);
     case 1024: return launch_global_p<1024, double>(a, maxD);

@@ -556,18 +556,35 @@ __device__ __forceinline__ void row_inv_half(bool active, const cplx<T> *src, in
 
 // --------------------------------------------------------- group plumbing
 
+// A thread's FFT group: GROUPS_PER_WARP groups of G consecutive lanes per
+// warp, numbered warp by warp.  When G does not divide 32 (G = 10) the last
+// lanes of each warp belong to no group: valid is false there, and they take
+// no task and touch no scratch.
 template <int P> struct GroupId {
     int group, t, lane;
     unsigned gmask;
+    bool valid;
     __device__ __forceinline__ GroupId(int tid)
     {
-        constexpr int G = FFTGeom<P>::G;
+        constexpr int G = FFTGeom<P>::G, GPW = FFTGeom<P>::GROUPS_PER_WARP;
         lane = tid & 31;
-        group = tid / G;
-        t = tid & (G - 1);
-        gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        if constexpr (FFTGeom<P>::POW2) {
+            valid = true;
+            group = tid / G;
+            t = tid & (G - 1);
+            gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        } else {
+            const int gw = lane / G;
+            valid = gw < GPW;
+            group = (tid >> 5) * GPW + gw;
+            t = lane - gw * G;
+            gmask = ((1u << G) - 1u) << (gw * G);
+        }
     }
 };
+
+// FFT groups of a block of NT threads (whole warps).
+template <int P, int NT> constexpr int groups_per_block() { return NT / 32 * FFTGeom<P>::GROUPS_PER_WARP; }
 
 // Fill the [R1][G] twiddle table exp(-2 pi i t k1 / P) from the length-P table.
 template <int P, typename T>

@@ -1,8 +1,10 @@
-"""The non-power-of-two padded grid P = 192 = 8 x 24 (ND_GRID_3X) for disks
-of 65..96 cells, against the FP64 oracle's direct sum: any P >= 2D - 1 gives
-the linear convolution exactly (the paper's power-of-two rule of Sec. II.B is
-a convenience), so the field, trajectories and relaxation sweeps must match
-the oracle to the same tolerances as on the power-of-two grids."""
+"""The non-power-of-two padded grids (ND_GRID_3X) P = 192 = 8 x 24 for disks
+of 65..96 cells and P = 200 = 10 x 20 (radix-5 register DFTs, ten-lane FFT
+groups) for disks of 97..100 cells, against the FP64 oracle's direct sum: any
+P >= 2D - 1 gives the linear convolution exactly (the paper's power-of-two
+rule of Sec. II.B is a convenience), so the field, trajectories and
+relaxation sweeps must match the oracle to the same tolerances as on the
+power-of-two grids."""
 import numpy as np
 import pytest
 
@@ -42,9 +44,25 @@ def test_grid192_field_matches_direct_sum(O, prec, R):
 
 
 @pytest.mark.parametrize("prec", [nd.ND_FP32, nd.ND_FP64])
-def test_grid192_trajectories_match_oracle(O, prec):
-    disk = Disk(90e-9, 10e-9, alpha=0.02)
+@pytest.mark.parametrize("R", [97e-9, 99e-9, 100e-9])   # D = 97 (the smallest, odd), 99, 100 (the largest)
+def test_grid200_field_matches_direct_sum(O, prec, R):
+    disk = Disk(R, 9e-9, hext=(1e4, 2e4, -1e4))
     h = Nanodisk([disk], [2], prec, grid3x=True)
+    assert h.layout[0]["P"] == 200
+    assert Nanodisk([disk], [1], prec).layout[0]["P"] == 256      # without the flag
+    model = O.Model(R, disk.L, hext=disk.hext)
+    grids = [ndsynth.random_unit_vectors(model.D, seed=s) * model.mask for s in (3, 4)]
+    b = h.unpack(h.field(h.to_device(grids)))
+    for g, bg in zip(grids, b):
+        assert rel(bg, model.field(g), model.mask) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [nd.ND_FP32, nd.ND_FP64])
+@pytest.mark.parametrize("R", [90e-9, 100e-9])                 # P = 192, 200
+def test_grid3x_trajectories_match_oracle(O, prec, R):
+    disk = Disk(R, 10e-9, alpha=0.02)
+    h = Nanodisk([disk], [2], prec, grid3x=True)
+    assert h.layout[0]["P"] == (192 if R < 97e-9 else 200)
     model = O.Model(disk.R, disk.L, alpha=disk.alpha)
     g = model.init_vortex(3e-9, -2e-9)
     dt = 1e-14
@@ -62,13 +80,14 @@ def test_grid192_trajectories_match_oracle(O, prec):
         assert traj_ok(out, ref, start, model.mask, prec, model.C)
 
 
-def test_grid192_relaxation_sweeps_and_mixed_classes(O):
-    """Relaxation sweeps on the P = 192 class inside a handle that also holds
-    an on-chip class (D = 30, P = 64) and a P = 256 class (D = 110)."""
-    ds = [Disk(30e-9, 10e-9), Disk(70e-9, 10e-9), Disk(110e-9, 10e-9)]
-    h = Nanodisk(ds, [1, 1, 1], nd.ND_FP32, grid3x=True)
-    assert [h.layout[r]["P"] for r in range(3)] == [64, 192, 256]
-    X = np.array([[2e-9, 0.0], [2.5e-9, 1e-9], [0.0, -2e-9]])
+def test_grid3x_relaxation_sweeps_and_mixed_classes(O):
+    """Relaxation sweeps on the P = 192 and P = 200 classes inside a handle
+    that also holds an on-chip class (D = 30, P = 64) and a P = 256 class
+    (D = 110)."""
+    ds = [Disk(30e-9, 10e-9), Disk(70e-9, 10e-9), Disk(110e-9, 10e-9), Disk(98e-9, 10e-9)]
+    h = Nanodisk(ds, [1, 1, 1, 1], nd.ND_FP32, grid3x=True)
+    assert [h.layout[r]["P"] for r in range(4)] == [64, 192, 256, 200]
+    X = np.array([[2e-9, 0.0], [2.5e-9, 1e-9], [0.0, -2e-9], [1.5e-9, 1.5e-9]])
     grids = [O.Model(d.R, d.L).init_vortex(0.0, 0.0) for d in ds]
     m = h.to_device(grids)
     rc, U, lam, it = h.relax(m, X, tol=1e-300, max_iter=3)
@@ -83,7 +102,7 @@ def test_grid192_relaxation_sweeps_and_mixed_classes(O):
         assert np.allclose(lam[r], lm, rtol=2e-3, atol=2e-3 * max(1e-3, np.abs(lm).max()))
     # a Heun step of every class
     m = h.to_device(grids)
-    h.heun(m, 2, 1e-14, [300.0] * 3, [7, 8, 9], step0=0)
+    h.heun(m, 2, 1e-14, [300.0] * 4, [7, 8, 9, 10], step0=0)
     out = h.unpack(m)
     for r, d in enumerate(ds):
         model = O.Model(d.R, d.L)
